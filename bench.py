@@ -1,0 +1,328 @@
+#!/usr/bin/env python
+"""Throughput of the FE-LBM contact-line step on GB300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl felbm|reference]
+
+A step is one full time step (collision, chemical potential with the wetting
+boundary, element Laplacian of mu, P0 forces, streaming right-hand side and
+the consistent-mass solve) of the 256x256 free droplet (131,585 grid points,
+131,072 unique nodes after periodic identification, 4 triangles per cell,
+jitter 0.25h, density ratio 100).  The metric is node-updates per second: one
+node, one step, both D2Q9 sets.  L2 is flushed before every timed step (a
+256 MiB write), each step is timed with CUDA events on the library's stream.
+
+The path has no exchange step across meshes, so N > 1 runs N independent
+replicas (one per GPU, weak scaling); value is the sum over ranks, the time
+the maximum over ranks.
+
+``--impl reference`` times the FP64 CPU oracle (numpy/scipy, one host core)
+on full-size steps of the same workload, capped to about two minutes.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+L2_FLUSH_BYTES = 256 << 20
+METRIC = "node-updates/s (2xD2Q9)"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="felbm", choices=["felbm", "reference"])
+    ap.add_argument("--cpu-baseline-only", action="store_true", help=argparse.SUPPRESS)
+    ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def workload():
+    from paper_1708_04678_gb300 import inputs as I
+    return I.free_droplet_256()
+
+
+# ------------------------------------------------------------- CPU oracle --
+def run_oracle(budget_s, max_steps, warmup):
+    """Time the FP64 oracle on full-size steps of the workload; returns
+    (node-updates/s, steps timed, seconds)."""
+    from oracle import OracleMesh, OracleSim, params_from_physical
+    w = workload()
+    m = w["mesh"]
+    sim = OracleSim(OracleMesh(m["xy"], m["tri"], m["wall_edges"], m["wall_id"], m["period"]),
+                    params_from_physical(w["phys"]), w["C0"])
+    for _ in range(warmup):
+        sim.step(1)
+    t0 = time.perf_counter()
+    n = 0
+    while n < max_steps:
+        sim.step(1)
+        n += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return len(m["xy"]) * n / dt, n, dt
+
+
+def cpu_baseline_subprocess(seconds):
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[k] = "1"
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-baseline-only",
+                        "--cpu-seconds", str(seconds)], capture_output=True, text=True, env=env)
+    if r.returncode != 0:
+        return {"error": r.stderr.strip().splitlines()[-1:] or ["failed"]}
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+# ----------------------------------------------------------------- clocks --
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.thread.join(timeout=2)
+
+    def summary(self):
+        sm = [float(r[1]) for r in self.rows if len(r) >= 9 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if len(r) >= 9 and r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in self.rows if len(r) >= 9
+                          for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(self.rows)}
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        try:
+            with open(path) as f:
+                d = json.load(f)
+            hbm = d.get("hbm_gbs") or d.get("hbm_GBps")
+            if hbm:
+                return float(hbm), "measured"
+        except (OSError, ValueError):
+            pass
+    return 6800.0, "fallback"
+
+
+# --------------------------------------------------------------- GPU arm --
+def run_gpu(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_1708_04678_gb300 import build as B
+    from paper_1708_04678_gb300 import felbm as F
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if rank == 0:
+        B.build()
+    if world > 1:
+        dist.barrier()
+    B.build()
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = cpu_baseline_subprocess(args.cpu_seconds)
+
+    w = workload()
+    N = len(w["mesh"]["xy"])
+    mesh = F.Mesh.from_dict(w["mesh"])
+    prm = F.params_derive(w["phys"])
+    stream = torch.cuda.Stream(dev)
+    st = F.State(mesh, prm, w["C0"], device=dev, stream=stream)
+    st.timing_enable(True)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    for k in range(max(args.warmup, 3)):
+        with torch.cuda.stream(stream):
+            flush.fill_(k & 255)
+        st.step(1)
+    stream.synchronize()
+
+    K = args.steps
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    phases = []
+    torch.cuda.synchronize()
+    barrier()
+    with ClockSampler(local) as clk:
+        for k in range(K):
+            with torch.cuda.stream(stream):
+                flush.fill_(k & 255)
+            ev0[k].record(stream)
+            st.step(1)
+            ev1[k].record(stream)
+            phases.append(st.timing_get())           # synchronises the stream
+        torch.cuda.synchronize()
+        barrier()
+    step_ms = [ev0[k].elapsed_time(ev1[k]) for k in range(K)]
+    total_ms = sum(step_ms)
+    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    total_ms = float(t.item())
+
+    # end to end through the public API with host buffers: pinned g, h in,
+    # one step, diagnostics (the step's metrics) out
+    g0, h0 = st.get_state()
+    gp = torch.from_numpy(g0).pin_memory()
+    hp = torch.from_numpy(h0).pin_memory()
+    for _ in range(2):
+        st.set_state(gp, hp)
+        st.step(1)
+        st.diagnostics()
+    torch.cuda.synchronize()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(K):
+        st.set_state(gp, hp)
+        st.step(1)
+        st.diagnostics()
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    e = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(e, op=dist.ReduceOp.MAX)
+    e2e_s = float(e.item())
+
+    if rank == 0:
+        ph = {k: statistics.mean(p[k] for p in phases) for k in phases[0] if k.endswith("_ms")}
+        launches = phases[0]["launches"]
+        solve_launches = phases[0]["solve_launches"]
+        info = mesh.info()
+        nnz = info["nnz"]
+        # dominant kernel: one Chebyshev sweep of the mass solve
+        sweep_ms = ph["solve_ms"] / solve_launches
+        # algorithmic bytes of one sweep: gathered x_k, own x_{k-1}, rhs, new x
+        # (4 x 18 doubles per node) + the mass row (column index, value) +
+        # row pointer and inverse lumped mass
+        alg_bytes = N * 4 * 18 * 8 + nnz * (4 + 8) + N * (4 + 8)
+        alg_flops = nnz * 18 * 2 + N * 18 * 6
+        hbm_peak, peak_src = peaks()
+        achieved_gbs = alg_bytes / (sweep_ms * 1e-3) / 1e9
+        value = N * K * world / (total_ms * 1e-3)
+        e2e_value = N * K * world / e2e_s
+        out = {
+            "metric": METRIC,
+            "value": value,
+            "unit": "node-updates/s",
+            "n_gpus": world,
+            "steps": K,
+            "warmup": max(args.warmup, 3),
+            "ms_per_step": total_ms / K,
+            "higher_is_better": True,
+            "scaling": "weak",
+            "vs_baseline": None,
+            "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": w["name"] + " free droplet, 131,585 grid points, 4 tri/cell, jitter 0.25h, FP64",
+                       "nodes": N, "triangles": info["n_tri"], "dt": w["phys"]["dt"],
+                       "solver_sweeps": solve_launches + 1, "l2": "flushed before every timed step (256 MiB write)",
+                       "parallelism": f"replicas x{world}"},
+            "phase_ms": {k: round(v, 5) for k, v in ph.items()},
+            "roofline": {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm_peak,
+                         "unit": "GB/s", "frac": achieved_gbs / hbm_peak, "traffic": None,
+                         "kernel": "k_cheb (one Chebyshev sweep of the 18-RHS mass solve)",
+                         "alg_bytes_per_launch": alg_bytes, "alg_flops_per_launch": alg_flops,
+                         "launch_ms": sweep_ms, "peak_source": peak_src},
+            "e2e": {"value": e2e_value, "unit": "node-updates/s",
+                    "h2d_bytes_per_step": 2 * 9 * N * 8, "d2h_bytes_per_step": 112},
+            "gpu_launches": launches * K,
+            "clocks": clk.summary(),
+        }
+        if cpu is not None:
+            out["cpu_baseline"] = cpu
+        print(json.dumps(out), flush=True)
+    st.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    budget = 120.0
+    v, n, secs = run_oracle(budget, args.steps, min(args.warmup, 1))
+    sample = (f"{n} full-size steps (after {min(args.warmup, 1)} warm-up) of the 131,072-node free droplet, "
+              f"{secs:.1f} s, stopped at the step that passed {budget:.0f} s")
+    out = {"metric": METRIC, "value": v, "unit": "node-updates/s", "n_gpus": 0, "steps": n,
+           "warmup": min(args.warmup, 1), "ms_per_step": secs * 1e3 / n, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": "free droplet 256x256, 131,585 grid points, 4 tri/cell, jitter 0.25h, FP64"},
+           "impl": "reference",
+           "cpu_baseline": {"value": v, "unit": "node-updates/s", "cores": 1, "kind": "oracle",
+                            "sample": sample},
+           "e2e": {"value": v, "unit": "node-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse()
+    if args.cpu_baseline_only:
+        v, n, secs = run_oracle(args.cpu_seconds, 10 ** 6, 1)
+        print(json.dumps({"value": v, "unit": "node-updates/s", "cores": 1, "kind": "oracle",
+                          "sample": f"{n} full-size steps of the 131,072-node free droplet after 1 warm-up, "
+                                    f"{secs:.1f} s, numpy/scipy single thread"}))
+        return
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,213 @@
+/*
+ * felbm.h -- C ABI of the GB300 FE-LBM contact-line step.
+ *
+ * One time step of the characteristic-based finite-element lattice Boltzmann
+ * method for the free-energy two-phase model with wetting walls
+ * (Matin, Misztal, Hernandez-Garcia, Mathiesen, arXiv:1708.04678), written
+ * for two D2Q9 distribution sets -- g (pressure/momentum) and h (composition)
+ * -- on unstructured linear triangles.  Every step of the update runs in CUDA
+ * kernels for sm_103a; the host only preprocesses the mesh once and enqueues.
+ *
+ * Conventions shared by every call:
+ *  - Return value: FELBM_OK (0) or a negative FELBM_ERR_* code; the message of
+ *    the last error of the calling thread is felbm_last_error().  No call
+ *    throws across the ABI.
+ *  - Host arrays are owned by the caller and only read (or written) during
+ *    the call.  Node numbering is the caller's: the library reorders nodes
+ *    internally (reverse Cuthill-McKee) and converts back on every exchange.
+ *  - Device memory: the library never allocates it.  The caller allocates one
+ *    workspace of felbm_workspace_bytes() bytes (any allocator, 256-byte
+ *    aligned) and keeps it alive until felbm_state_destroy().
+ *  - Streams: all device work of a state is enqueued on the cudaStream_t given
+ *    to felbm_init (passed as void*; NULL = legacy default stream).  Calls
+ *    that return host data synchronise that stream; felbm_step does not.
+ *  - Distribution layout on the host: double [9][n_nodes], direction-major,
+ *    D2Q9 order e_0 = (0,0), e_1..e_4 = (1,0),(0,1),(-1,0),(0,-1),
+ *    e_5..e_8 = (1,1),(-1,1),(-1,-1),(1,-1); weights 4/9, 1/9, 1/36.
+ */
+#ifndef FELBM_H
+#define FELBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FELBM_OK 0
+#define FELBM_ERR_INVALID_ARG (-1)
+#define FELBM_ERR_BAD_MESH (-2)     /* inverted/degenerate triangle, open edge that is no wall, ... */
+#define FELBM_ERR_CUDA (-3)         /* a CUDA runtime call failed */
+#define FELBM_ERR_WORKSPACE (-4)    /* workspace missing, misaligned or too small */
+#define FELBM_ERR_NONFINITE (-5)    /* NaN or Inf found in the state */
+#define FELBM_ERR_UNSUPPORTED (-6)  /* option not available in this build */
+
+#define FELBM_MAX_WALL_IDS 8
+
+/* Patch Laplacian of C (eqn:lapl_int_mp): V = 2/3 |patch| (equals the lumped
+ * P1 Laplacian) or V = |patch| (the literal patch area). */
+#define FELBM_LAP_CONSISTENT 0
+#define FELBM_LAP_PAPER 1
+
+/* Storage/arithmetic of the distributions. */
+#define FELBM_FP64 0
+
+/* Model constants (Sec. II of the paper, lattice units).
+ *  dt              time step (characteristic step eqn::integrated)
+ *  tau_l, tau_v    relaxation times of liquid and vapour; 1/tau = C/tau_l + (1-C)/tau_v
+ *  rho_l, rho_v    bulk densities; rho = C rho_l + (1-C) rho_v
+ *  kappa, beta     gradient and bulk free-energy constants (eqn:FE_func_b)
+ *  mobility        Cahn-Hilliard mobility M (eqn:mp_che)
+ *  phi_c[id]       wetting potential of wall id (eqn:bc2); cos(theta) = -phi_c / sqrt(2 kappa beta)
+ *  lap_mode        FELBM_LAP_CONSISTENT or FELBM_LAP_PAPER
+ *  precision       FELBM_FP64
+ *  solver_iters    Chebyshev sweeps of the mass-matrix solve (0 = 32: error
+ *                  bound 2*3^-32 relative in the energy norm)            */
+typedef struct felbm_params {
+    double dt;
+    double tau_l, tau_v;
+    double rho_l, rho_v;
+    double kappa, beta;
+    double mobility;
+    double phi_c[FELBM_MAX_WALL_IDS];
+    int32_t n_wall_ids;
+    int32_t lap_mode;
+    int32_t precision;
+    int32_t solver_iters;
+} felbm_params;
+
+typedef struct felbm_mesh felbm_mesh;
+typedef struct felbm_state felbm_state;
+
+typedef struct felbm_mesh_info {
+    int32_t n_nodes, n_tri, n_wall_edges;
+    int32_t nnz;              /* entries of the node-node sparsity pattern */
+    int32_t max_degree;       /* largest row of that pattern */
+    int32_t bandwidth;        /* after reverse Cuthill-McKee */
+    double min_area, total_area;
+} felbm_mesh_info;
+
+/* What felbm_diagnostics measures beside the global sums. */
+typedef struct felbm_diag_request {
+    double centre[2];         /* droplet centre for the interface band */
+    double radius;            /* droplet radius R; band = nodes with |r - R| <= band */
+    double band;              /* half width of the band (the paper uses xi) */
+    int32_t substrate_wall_id;/* wall id on which contact angle is measured; <0: none */
+} felbm_diag_request;
+
+typedef struct felbm_diag {
+    int64_t step;
+    double mass;              /* sum_i m_i C_i, m_i = lumped mass (= |patch_i|/3) */
+    double mass0;             /* the same at felbm_init */
+    double mass_drift_rel;    /* (mass - mass0) / mass0 */
+    double kinetic_energy;    /* <T> = 1/2 sum_i rho_i |u_i|^2 / N (Fig. 5 caption) */
+    double max_u;             /* max_i |u_i| (spurious-current magnitude) */
+    double interface_rho_uu;  /* area-weighted mean of rho |u|^2 over the band (Table I) */
+    double p_in, p_out;       /* area-weighted mean p over C >= 0.95 / C <= 0.05 */
+    double delta_p;           /* p_in - p_out (Laplace jump) */
+    double wetted_length;     /* length of substrate wall edges with C >= 1/2 (linear in C) */
+    double height;            /* max height of the C = 1/2 contour above the mean substrate height */
+    double theta_deg;         /* contact angle from height and base, circular cap (Sec. III.B) */
+    int32_t status;           /* FELBM_OK or FELBM_ERR_NONFINITE */
+} felbm_diag;
+
+/* Text of the calling thread's last error ("" if none). */
+const char* felbm_last_error(void);
+
+/* Fill kappa, beta and phi_c[0..n_wall_ids) of *p from the surface tension
+ * sigma, the interface width xi and the contact angles (degrees):
+ * xi = sqrt(8 kappa/beta), sigma = sqrt(2 kappa beta)/6 (Sec. II, planar
+ * profile) and cos(theta) = -phi_c/sqrt(2 kappa beta) (Sec. II.B, Young). */
+int felbm_params_derive(double sigma, double xi, const double* theta_deg,
+                        int32_t n_wall_ids, felbm_params* p);
+
+/* Build a mesh (host only; Sec. II.C, linear elements).
+ *  xy          double [n_nodes][2] node coordinates
+ *  tri         int32 [n_tri][3] node ids, counter-clockwise after minimum image
+ *  wall_edges  int32 [n_wall_edges][2] node pairs lying on solid walls
+ *  wall_id     int32 [n_wall_edges] index into felbm_params.phi_c
+ *  period_x/y  periodic lengths (0 = not periodic); periodic images are one node
+ * Every edge used by one triangle only must be a wall edge.  Errors:
+ * FELBM_ERR_INVALID_ARG (bad sizes/ids), FELBM_ERR_BAD_MESH (non-positive
+ * area, open edge that is not a wall, wall edge that is not a boundary edge,
+ * edge shared by more than two triangles).  *out is freed by felbm_mesh_destroy. */
+int felbm_mesh_create(const double* xy, int32_t n_nodes, const int32_t* tri, int32_t n_tri,
+                      const int32_t* wall_edges, const int32_t* wall_id, int32_t n_wall_edges,
+                      double period_x, double period_y, felbm_mesh** out);
+int felbm_mesh_info_get(const felbm_mesh* mesh, felbm_mesh_info* out);
+void felbm_mesh_destroy(felbm_mesh* mesh);
+
+/* Bytes of device workspace a state of this mesh and these params needs. */
+int felbm_workspace_bytes(const felbm_mesh* mesh, const felbm_params* params, size_t* bytes);
+
+/* Create a state on the device: upload the mesh tables into the workspace and
+ * set g = w p, h = w C from C0 (double [n_nodes], host) with p = 0, u = 0 --
+ * the equilibria at rest (eqn::g_eq, eqn::f_eq).  d_workspace: device
+ * pointer, 256-byte aligned, >= felbm_workspace_bytes.  stream: cudaStream_t.
+ * The mesh may be destroyed after this call.  Synchronises the stream. */
+int felbm_init(const felbm_mesh* mesh, const felbm_params* params, const double* C0,
+               void* d_workspace, size_t workspace_bytes, void* stream, felbm_state** out);
+
+/* Enqueue n_steps time steps (Sec. II.C): moments, chemical potential with the
+ * wetting boundary (eqn:mp_mu, eqn:lapl_int_mp, eqn:bc2), element Laplacian of
+ * mu (Sec. II.D), P0 forces at the barycentre (eq:G, eq:H, eq:intF),
+ * collision (eqn::collide), weak-form streaming right-hand side
+ * (eq:galerkin_lbm, force term +(dt M10 + dt^2 K) Phi, weak bounce-back at
+ * walls) and the consistent-mass solve, all as one CUDA graph per step on the
+ * state's stream.  Does not synchronise. */
+int felbm_step(felbm_state* state, int32_t n_steps);
+
+/* Reduce the diagnostics of Sec. III on the device (deterministic FP64
+ * reductions) and copy them to *out.  req may be NULL (no band, substrate 0).
+ * Synchronises the stream.  Returns FELBM_ERR_NONFINITE (and fills *out) if
+ * the state holds a NaN or Inf. */
+int felbm_diagnostics(felbm_state* state, const felbm_diag_request* req, felbm_diag* out);
+
+/* Copy the distributions out / in: g, h double [9][n_nodes] host, caller order.
+ * Pinned host memory makes the copies asynchronous DMA.  Both synchronise. */
+int felbm_get_state(felbm_state* state, double* g, double* h);
+int felbm_set_state(felbm_state* state, const double* g, const double* h);
+
+/* Nodal fields of the last step's start (moments of the pre-collision state
+ * and the chemical potential): each double [n_nodes] host, caller order, any
+ * may be NULL.  Recomputes them from the current state first.  Synchronises. */
+int felbm_get_fields(felbm_state* state, double* C, double* p, double* ux, double* uy, double* mu);
+
+/* Solve M11 X = B for k right-hand sides with the state's mass matrix and
+ * the same Chebyshev iteration felbm_step uses (Sec. II.C: consistent mass
+ * matrix, lumped-mass preconditioner).  B, X: double [k][n_nodes] host,
+ * caller order; 1 <= k <= 18.  Uses the state's scratch buffers; do not
+ * overlap with felbm_step on another stream.  Synchronises. */
+int felbm_mass_solve(felbm_state* state, const double* B, double* X, int32_t k);
+
+/* Device time of the phases of one time step, milliseconds, from CUDA events
+ * recorded inside the step's graph (instrumentation, not part of the method). */
+typedef struct felbm_step_timing {
+    float collide_ms;   /* moments and collision */
+    float mu_ms;        /* chemical potential with the wetting flux */
+    float gradmu_ms;    /* P0 gradient of mu */
+    float element_ms;   /* element Laplacian of mu, forces, element residual */
+    float rhs_ms;       /* streaming right-hand-side gather */
+    float solve_ms;     /* all sweeps of the mass solve */
+    float total_ms;
+    int32_t solve_launches;  /* kernel launches inside solve_ms */
+    int32_t launches;        /* kernel launches of one step */
+} felbm_step_timing;
+
+/* Switch the per-phase events on or off; the step graph is rebuilt at the
+ * next felbm_step.  Off by default. */
+int felbm_timing_enable(felbm_state* state, int32_t enable);
+
+/* Phase times of the most recent felbm_step launch of the graph (the last of
+ * its n_steps).  Synchronises the stream.  FELBM_ERR_INVALID_ARG if timing
+ * is off or no step ran since it was switched on. */
+int felbm_timing_get(felbm_state* state, felbm_step_timing* out);
+
+/* Release the host-side state object (the caller frees the workspace). */
+void felbm_state_destroy(felbm_state* state);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FELBM_H */

@@ -1,0 +1,1111 @@
+// CUDA implementation of the FE-LBM contact-line step for sm_103a (GB300).
+//
+// Data layout in HBM (all carved from the caller's workspace):
+//  * distributions psi: double [18][Np] -- g_0..g_8 then h_0..h_8, direction
+//    major, node stride Np = N rounded up to 64 (coalesced node streams);
+//  * nodal fields C, p, ux, uy, mu: double [Np];
+//  * triangle tables: vertices int [3][Tp], area [Tp], shape gradients
+//    double [6][Tp], edge neighbours int [3][Tp] (structure of arrays);
+//  * element residual R: double [T][18] (array of structures: the node gather
+//    reads one triangle's 18 values as 9 contiguous 16-byte loads);
+//  * node-node pattern (CSR) with the consistent mass and Laplacian
+//    coefficients; node -> triangle and node -> wall-edge incidence (CSR).
+// Nodes are in reverse Cuthill-McKee order and triangles sorted by their
+// lowest node, so every gather reads a narrow window of the arrays.
+//
+// One time step (Sec. II.C of arXiv:1708.04678, D2Q9 form) is six kinds of
+// kernels, captured once into a CUDA graph:
+//   k_collide   moments (eq:velocity, eq:pressure), collision (eqn::collide)
+//   k_mu        chemical potential with the patch Laplacian and the wetting
+//               flux (eqn:mp_mu, eqn:lapl_int_mp, eqn:bc2)
+//   k_gradmu    P0 gradient of mu per triangle
+//   k_element   element Laplacian of mu (Sec. II.D), P0 forces at the
+//               barycentre (eq:G, eq:H, eq:intF) and the element residual
+//               A_T (Phi - e.grad psi_hat) of eq:galerkin_lbm
+//   k_rhs       node-centric gather of the streaming right-hand side with
+//               weak bounce-back on walls; first Chebyshev iterate
+//   k_cheb      Chebyshev sweeps of the consistent-mass solve with the
+//               lumped-mass preconditioner; the last adds the increment
+// No atomics anywhere: every sum is a fixed-order loop or tree.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "felbm_internal.h"
+
+namespace felbm {
+
+// ---------------------------------------------------------------- D2Q9 ----
+__host__ __device__ constexpr int ex(int q) {
+    return q == 1 || q == 5 || q == 8 ? 1 : (q == 3 || q == 6 || q == 7 ? -1 : 0);
+}
+__host__ __device__ constexpr int ey(int q) {
+    return q == 2 || q == 5 || q == 6 ? 1 : (q == 4 || q == 7 || q == 8 ? -1 : 0);
+}
+__host__ __device__ constexpr double wq(int q) {
+    return q == 0 ? 4.0 / 9.0 : (q <= 4 ? 1.0 / 9.0 : 1.0 / 36.0);
+}
+__host__ __device__ constexpr int opp(int q) {
+    return q == 0 ? 0 : (q <= 4 ? (q + 1) % 4 + 1 : (q - 5 + 2) % 4 + 5);
+}
+static_assert(opp(1) == 3 && opp(2) == 4 && opp(3) == 1 && opp(4) == 2, "opp");
+static_assert(opp(5) == 7 && opp(6) == 8 && opp(7) == 5 && opp(8) == 6, "opp");
+
+// e.v for a compile-time direction: only additions
+template <int q>
+__device__ __forceinline__ double edot(double vx, double vy) {
+    double r = 0.0;
+    if (ex(q) == 1) r = vx;
+    if (ex(q) == -1) r = -vx;
+    if (ey(q) == 1) r = r + vy;
+    if (ey(q) == -1) r = r - vy;
+    return r;
+}
+
+// ------------------------------------------------------- device tables ----
+struct DevMesh {
+    int32_t N, T, E, Np, Tp;
+    double period_y;
+    const int32_t* tri;       // [3][Tp]
+    const double* area;       // [Tp]
+    const double* grad;       // [6][Tp]
+    const int32_t* nbr;       // [3][Tp]
+    const int32_t* row_ptr;   // [N+1]
+    const int32_t* col;       // [nnz]
+    const double* mval;       // [nnz] consistent mass
+    const double* lval;       // [nnz] -2 K_ij / V_i (patch Laplacian of C)
+    const double* inv_lumped; // [Np]
+    const double* lumped;     // [Np]
+    const double* inv_vol;    // [Np] 1 / V_i
+    const int32_t* inc_ptr;   // [N+1]
+    const int32_t* inc_tri;   // [ninc]
+    const double* inc_bx;     // [ninc]
+    const double* inc_by;     // [ninc]
+    const int32_t* wall_a;    // [E]
+    const int32_t* wall_b;
+    const int32_t* wall_id;
+    const double* wall_len;
+    const double* wall_nx;
+    const double* wall_ny;
+    const int32_t* winc_ptr;  // [N+1]
+    const int32_t* winc_edge;
+    const double* x;          // [Np]
+    const double* y;
+    const int32_t* perm;      // [N] new -> caller
+    const int32_t* iperm;     // [N] caller -> new
+};
+
+struct Phys {
+    double dt, tau_l, tau_v, rho_l, rho_v, kappa, beta, mobility;
+    double phi_c[FELBM_MAX_WALL_IDS];
+};
+
+struct Bufs {
+    double* psi;     // [18][Np]
+    double* C;       // [Np]
+    double* p;
+    double* ux;
+    double* uy;
+    double* mu;
+    double* gmu;     // [2][Tp]
+    double* R;       // [T][18]
+    double* rhs;     // [18][Np]
+    double* x0;      // [18][Np]
+    double* x1;      // [18][Np]
+    double* stage;   // [18][Np] caller-order staging
+    double* diag_part; // [kDiagBlocks][kDiagSlots]
+    double* diag_out;  // [kDiagSlots]
+    double* Cdiag;     // [Np]
+};
+
+constexpr int kBlock = 256;
+constexpr int kDiagBlocks = 304;   // fixed grid (2 x 152 SMs): the reduction order never changes
+constexpr int kDiagSlots = 16;
+
+// ------------------------------------------------------ K1: collision -----
+// Moments of the pre-collision state (C = sum h, p = sum g, rho u = sum e g /
+// cs2) and BGK collision towards the equilibria of eqn::g_eq / eqn::f_eq,
+// written in place: g_eq = w p + rho cs2 (Gamma - w), h_eq = Gamma C.
+__global__ void __launch_bounds__(kBlock) k_collide(DevMesh m, Phys c, Bufs b, int do_collide) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m.N) return;
+    const int Np = m.Np;
+    double g[9], h[9];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) {
+        g[q] = b.psi[q * Np + i];
+        h[q] = b.psi[(9 + q) * Np + i];
+    }
+    double C = 0.0, p = 0.0;
+#pragma unroll
+    for (int q = 0; q < 9; ++q) {
+        C += h[q];
+        p += g[q];
+    }
+    double mx = (g[1] - g[3]) + (g[5] - g[6]) + (g[8] - g[7]);
+    double my = (g[2] - g[4]) + (g[5] + g[6]) - (g[7] + g[8]);
+    double rho = c.rho_v + C * (c.rho_l - c.rho_v);
+    double ux = 3.0 * mx / rho, uy = 3.0 * my / rho;
+    b.C[i] = C;
+    b.p[i] = p;
+    b.ux[i] = ux;
+    b.uy[i] = uy;
+    if (!do_collide) return;
+    double inv_tau = C / c.tau_l + (1.0 - C) / c.tau_v;
+    double omega = 1.0 / (1.0 / inv_tau + 0.5);
+    double uu15 = 1.5 * (ux * ux + uy * uy);
+    double rcs2 = rho * (1.0 / 3.0);
+#define FELBM_COLLIDE_Q(q)                                                            \
+    {                                                                                 \
+        double eu = edot<q>(ux, uy);                                                  \
+        double G = wq(q) * (1.0 + 3.0 * eu + 4.5 * eu * eu - uu15);                   \
+        double geq = wq(q) * p + rcs2 * (G - wq(q));                                  \
+        double heq = G * C;                                                           \
+        b.psi[q * Np + i] = g[q] - omega * (g[q] - geq);                              \
+        b.psi[(9 + q) * Np + i] = h[q] - omega * (h[q] - heq);                        \
+    }
+    FELBM_COLLIDE_Q(0) FELBM_COLLIDE_Q(1) FELBM_COLLIDE_Q(2) FELBM_COLLIDE_Q(3)
+    FELBM_COLLIDE_Q(4) FELBM_COLLIDE_Q(5) FELBM_COLLIDE_Q(6) FELBM_COLLIDE_Q(7)
+    FELBM_COLLIDE_Q(8)
+#undef FELBM_COLLIDE_Q
+}
+
+// --------------------------------------------- K2: chemical potential -----
+// mu_i = 2 beta C (C-1)(2C-1) - kappa lap(C)_i with the patch Laplacian
+// kappa lap(C)_i = kappa sum_j l_ij C_j + (1/V_i) sum_{wall e at i} -phi_c |e|
+// [ (Ca+Cb)/2 - (Ca^2 + Ca Cb + Cb^2)/3 ]  (wall flux of eqn:bc2, C linear on e).
+__global__ void __launch_bounds__(kBlock) k_mu(DevMesh m, Phys c, Bufs b) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m.N) return;
+    double lap = 0.0;
+    for (int k = m.row_ptr[i]; k < m.row_ptr[i + 1]; ++k) lap += m.lval[k] * b.C[m.col[k]];
+    double wall = 0.0;
+    for (int k = m.winc_ptr[i]; k < m.winc_ptr[i + 1]; ++k) {
+        int e = m.winc_edge[k];
+        double Ca = b.C[m.wall_a[e]], Cb = b.C[m.wall_b[e]];
+        double s = 0.5 * (Ca + Cb) - (Ca * Ca + Ca * Cb + Cb * Cb) * (1.0 / 3.0);
+        wall -= c.phi_c[m.wall_id[e]] * m.wall_len[e] * s;
+    }
+    double C = b.C[i];
+    b.mu[i] = 2.0 * c.beta * C * (C - 1.0) * (2.0 * C - 1.0) - (c.kappa * lap + wall * m.inv_vol[i]);
+}
+
+// ------------------------------------------------- K3: grad mu per T ------
+__global__ void __launch_bounds__(kBlock) k_gradmu(DevMesh m, Bufs b) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= m.T) return;
+    const int Tp = m.Tp;
+    double gx = 0.0, gy = 0.0;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        double mu = b.mu[m.tri[k * Tp + t]];
+        gx += mu * m.grad[(2 * k) * Tp + t];
+        gy += mu * m.grad[(2 * k + 1) * Tp + t];
+    }
+    b.gmu[t] = gx;
+    b.gmu[Tp + t] = gy;
+}
+
+// ------------------------------- K4: forces and element residual ---------
+// lap(mu)_T = (1/A) sum_{interior edges} 1/2 (grad mu_T + grad mu_T').nu_k with
+// nu_k = -2 A b_k (outward normal x length of the edge opposite vertex k);
+// wall edges give 0 (eqn:bc1).  Forces at the barycentre:
+//   Phi_g = (e-u).[cs2 grad(rho) (Gamma - w) + mu grad(C) Gamma]
+//   Phi_h = [(e-u).(grad C - C/(rho cs2) (grad p - mu grad C)) + M lap(mu)] Gamma
+// Residual R_a = A (Phi_a - e_a . grad psi_hat_a), psi_hat P1 on the triangle.
+__global__ void __launch_bounds__(128) k_element(DevMesh m, Phys c, Bufs b) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= m.T) return;
+    const int Tp = m.Tp, Np = m.Np;
+    int v[3];
+    double bx[3], by[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        v[k] = m.tri[k * Tp + t];
+        bx[k] = m.grad[(2 * k) * Tp + t];
+        by[k] = m.grad[(2 * k + 1) * Tp + t];
+    }
+    const double A = m.area[t];
+    double Cs = 0, ps = 0, uxs = 0, uys = 0, mus = 0, gCx = 0, gCy = 0, gpx = 0, gpy = 0;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        double Cv = b.C[v[k]], pv = b.p[v[k]];
+        Cs += Cv;
+        ps += pv;
+        uxs += b.ux[v[k]];
+        uys += b.uy[v[k]];
+        mus += b.mu[v[k]];
+        gCx += Cv * bx[k];
+        gCy += Cv * by[k];
+        gpx += pv * bx[k];
+        gpy += pv * by[k];
+    }
+    const double third = 1.0 / 3.0;
+    double Cb = Cs * third, ux = uxs * third, uy = uys * third, mub = mus * third;
+    double gmx = b.gmu[t], gmy = b.gmu[Tp + t];
+    double lapmu = 0.0;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        int nb = m.nbr[k * Tp + t];
+        if (nb >= 0) lapmu -= (gmx + b.gmu[nb]) * bx[k] + (gmy + b.gmu[Tp + nb]) * by[k];
+    }
+    double drho = c.rho_l - c.rho_v;
+    double rhob = c.rho_v + Cb * drho;
+    double grx = drho * gCx, gry = drho * gCy;
+    double f = 3.0 * Cb / rhob;
+    double vhx = gCx - f * (gpx - mub * gCx), vhy = gCy - f * (gpy - mub * gCy);
+    double u_gr = ux * grx + uy * gry, u_gC = ux * gCx + uy * gCy, u_vh = ux * vhx + uy * vhy;
+    double uu15 = 1.5 * (ux * ux + uy * uy);
+    double Mlap = c.mobility * lapmu;
+    double out[18];
+#define FELBM_ELEM_Q(q)                                                                           \
+    {                                                                                             \
+        double eu = edot<q>(ux, uy);                                                              \
+        double G = wq(q) * (1.0 + 3.0 * eu + 4.5 * eu * eu - uu15);                               \
+        double phig = third * (G - wq(q)) * (edot<q>(grx, gry) - u_gr) + mub * G * (edot<q>(gCx, gCy) - u_gC); \
+        double phih = ((edot<q>(vhx, vhy) - u_vh) + Mlap) * G;                                    \
+        double dg = 0.0, dh = 0.0;                                                                \
+        if (q != 0) {                                                                             \
+            for (int k = 0; k < 3; ++k) {                                                         \
+                double eb = edot<q>(bx[k], by[k]);                                                \
+                dg += b.psi[q * Np + v[k]] * eb;                                                  \
+                dh += b.psi[(9 + q) * Np + v[k]] * eb;                                            \
+            }                                                                                     \
+        }                                                                                         \
+        out[q] = A * (phig - dg);                                                                 \
+        out[9 + q] = A * (phih - dh);                                                             \
+    }
+    FELBM_ELEM_Q(0) FELBM_ELEM_Q(1) FELBM_ELEM_Q(2) FELBM_ELEM_Q(3) FELBM_ELEM_Q(4)
+    FELBM_ELEM_Q(5) FELBM_ELEM_Q(6) FELBM_ELEM_Q(7) FELBM_ELEM_Q(8)
+#undef FELBM_ELEM_Q
+    double2* dst = reinterpret_cast<double2*>(b.R + (size_t)t * 18);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) dst[k] = make_double2(out[2 * k], out[2 * k + 1]);
+}
+
+// ------------------------------------------- K5: streaming RHS gather -----
+// RHS_{i,a} = sum_{T at i} R_{T,a} (dt/3 + dt^2/2 e_a.b_{i,T})
+//           - dt sum_{wall e at i} (e_a.n) [L/3 (psi_opp - psi)_i + L/6 (psi_opp - psi)_o]
+// (second sum only for incoming directions e_a.n < 0; o = other end of e).
+// Also writes the first Chebyshev iterate x1 = RHS / (m_i theta).
+__global__ void __launch_bounds__(128) k_rhs(DevMesh m, Phys c, Bufs b, double inv_theta) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m.N) return;
+    const int Np = m.Np;
+    double acc[18];
+#pragma unroll
+    for (int q = 0; q < 18; ++q) acc[q] = 0.0;
+    const double c1 = c.dt * (1.0 / 3.0), c2 = 0.5 * c.dt * c.dt;
+    for (int k = m.inc_ptr[i]; k < m.inc_ptr[i + 1]; ++k) {
+        int t = m.inc_tri[k];
+        double bxi = m.inc_bx[k], byi = m.inc_by[k];
+        const double2* src = reinterpret_cast<const double2*>(b.R + (size_t)t * 18);
+        double r[18];
+#pragma unroll
+        for (int s = 0; s < 9; ++s) {
+            double2 v2 = src[s];
+            r[2 * s] = v2.x;
+            r[2 * s + 1] = v2.y;
+        }
+#define FELBM_RHS_Q(q)                                          \
+        {                                                       \
+            double w = c1 + c2 * edot<q>(bxi, byi);             \
+            acc[q] += r[q] * w;                                 \
+            acc[9 + q] += r[9 + q] * w;                         \
+        }
+        FELBM_RHS_Q(0) FELBM_RHS_Q(1) FELBM_RHS_Q(2) FELBM_RHS_Q(3) FELBM_RHS_Q(4)
+        FELBM_RHS_Q(5) FELBM_RHS_Q(6) FELBM_RHS_Q(7) FELBM_RHS_Q(8)
+#undef FELBM_RHS_Q
+    }
+    for (int k = m.winc_ptr[i]; k < m.winc_ptr[i + 1]; ++k) {
+        int e = m.winc_edge[k];
+        int o = m.wall_a[e] == i ? m.wall_b[e] : m.wall_a[e];
+        double L = m.wall_len[e], nx = m.wall_nx[e], ny = m.wall_ny[e];
+#define FELBM_WALL_Q(q)                                                                      \
+        {                                                                                    \
+            double en = edot<q>(nx, ny);                                                     \
+            if (en < 0.0) {                                                                  \
+                double f = -c.dt * en;                                                       \
+                double dgi = b.psi[opp(q) * Np + i] - b.psi[q * Np + i];                     \
+                double dgo = b.psi[opp(q) * Np + o] - b.psi[q * Np + o];                     \
+                double dhi = b.psi[(9 + opp(q)) * Np + i] - b.psi[(9 + q) * Np + i];         \
+                double dho = b.psi[(9 + opp(q)) * Np + o] - b.psi[(9 + q) * Np + o];         \
+                acc[q] += f * (L * (1.0 / 3.0) * dgi + L * (1.0 / 6.0) * dgo);               \
+                acc[9 + q] += f * (L * (1.0 / 3.0) * dhi + L * (1.0 / 6.0) * dho);           \
+            }                                                                                \
+        }
+        FELBM_WALL_Q(1) FELBM_WALL_Q(2) FELBM_WALL_Q(3) FELBM_WALL_Q(4)
+        FELBM_WALL_Q(5) FELBM_WALL_Q(6) FELBM_WALL_Q(7) FELBM_WALL_Q(8)
+#undef FELBM_WALL_Q
+    }
+    double s = m.inv_lumped[i] * inv_theta;
+#pragma unroll
+    for (int q = 0; q < 18; ++q) {
+        b.rhs[q * Np + i] = acc[q];
+        b.x1[q * Np + i] = acc[q] * s;
+    }
+}
+
+// First Chebyshev iterate for a standalone solve: x1 = B / (m_i theta).
+__global__ void __launch_bounds__(kBlock) k_cheb_start(DevMesh m, Bufs b, double inv_theta) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m.N) return;
+    const int Np = m.Np;
+    double s = m.inv_lumped[i] * inv_theta;
+#pragma unroll
+    for (int q = 0; q < 18; ++q) b.x1[q * Np + i] = b.rhs[q * Np + i] * s;
+}
+
+// ---------------------------------------------- K6: Chebyshev sweep -------
+// x_{k+1} = x_k + a (x_k - x_{k-1}) + c m^{-1} (b - M x_k), the three-term
+// Chebyshev recurrence for the lumped-mass preconditioned consistent mass
+// matrix, whose spectrum lies in [1/4, 1] on any P1 triangulation.
+//   cur  = x_k (gathered), prev = x_{k-1} (own node only; ignored if first),
+//   the new iterate overwrites prev, or is added to psi on the last sweep.
+__global__ void __launch_bounds__(128) k_cheb(DevMesh m, Bufs b, const double* __restrict__ cur,
+                                              double* prev, double a, double cc, int first,
+                                              int add_to_psi) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m.N) return;
+    const int Np = m.Np;
+    double acc[18];
+#pragma unroll
+    for (int q = 0; q < 18; ++q) acc[q] = 0.0;
+    for (int k = m.row_ptr[i]; k < m.row_ptr[i + 1]; ++k) {
+        int j = m.col[k];
+        double mv = m.mval[k];
+#pragma unroll
+        for (int q = 0; q < 18; ++q) acc[q] += mv * cur[q * Np + j];
+    }
+    double s = cc * m.inv_lumped[i];
+#pragma unroll
+    for (int q = 0; q < 18; ++q) {
+        double xk = cur[q * Np + i];
+        double xm = first ? 0.0 : prev[q * Np + i];
+        double xn = xk + a * (xk - xm) + s * (b.rhs[q * Np + i] - acc[q]);
+        if (add_to_psi)
+            b.psi[q * Np + i] += xn;
+        else
+            prev[q * Np + i] = xn;
+    }
+}
+
+// ----------------------------------------------- permutation kernels ------
+__global__ void k_scatter_in(DevMesh m, const double* __restrict__ stage, double* dst, int rows) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m.N) return;
+    int o = m.perm[i];
+    for (int q = 0; q < rows; ++q) dst[q * m.Np + i] = stage[(size_t)q * m.N + o];
+}
+__global__ void k_gather_out(DevMesh m, const double* __restrict__ src, double* stage, int rows) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m.N) return;
+    int o = m.perm[i];
+    for (int q = 0; q < rows; ++q) stage[(size_t)q * m.N + o] = src[q * m.Np + i];
+}
+__global__ void k_zero_rows(DevMesh m, double* dst, int row0, int row1) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m.N) return;
+    for (int q = row0; q < row1; ++q) dst[q * m.Np + i] = 0.0;
+}
+// initial state at rest: g = w p (p = 0), h = w C0
+__global__ void k_init_state(DevMesh m, const double* __restrict__ stage, double* psi) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m.N) return;
+    double C = stage[m.perm[i]];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) {
+        psi[q * m.Np + i] = 0.0;
+        psi[(9 + q) * m.Np + i] = wq(q) * C;
+    }
+}
+
+// ------------------------------------------------------ diagnostics -------
+// Slots: 0 mass, 1 sum rho|u|^2, 2 band weight, 3 band sum m rho|u|^2,
+// 4 liquid weight, 5 liquid sum m p, 6 vapour weight, 7 vapour sum m p,
+// 8 unused, 9 non-finite count, 10 max |u|^2 (node pass);
+// 11 wetted length, 12 max contour height (edge pass).
+struct DiagReq {
+    double cx, cy, R, band;
+    double period_x, period_y;
+    int substrate;
+    int use_band;
+};
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+    return v;
+}
+
+__device__ __forceinline__ double min_image(double d, double L) {
+    return L > 0.0 ? d - L * rint(d / L) : d;
+}
+
+template <int NS, int NM>
+__device__ void block_reduce_store(double (&s)[NS], double (&mx)[NM], double* out) {
+    __shared__ double sh[kBlock / 32][NS + NM];
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < NS; ++k) s[k] = warp_sum(s[k]);
+#pragma unroll
+    for (int k = 0; k < NM; ++k) mx[k] = warp_max(mx[k]);
+    if (lane == 0) {
+#pragma unroll
+        for (int k = 0; k < NS; ++k) sh[wid][k] = s[k];
+#pragma unroll
+        for (int k = 0; k < NM; ++k) sh[wid][NS + k] = mx[k];
+    }
+    __syncthreads();
+    if (threadIdx.x < NS + NM) {
+        int k = threadIdx.x;
+        double r = sh[0][k];
+        for (int w = 1; w < kBlock / 32; ++w) r = k < NS ? r + sh[w][k] : fmax(r, sh[w][k]);
+        out[k] = r;
+    }
+}
+
+__global__ void __launch_bounds__(kBlock) k_diag_nodes(DevMesh m, Phys c, Bufs b, DiagReq rq) {
+    double s[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    double mx[1] = {0.0};
+    const int Np = m.Np;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m.N; i += gridDim.x * blockDim.x) {
+        double C = 0, p = 0, g[9];
+#pragma unroll
+        for (int q = 0; q < 9; ++q) {
+            g[q] = b.psi[q * Np + i];
+            p += g[q];
+            C += b.psi[(9 + q) * Np + i];
+        }
+        double mxm = (g[1] - g[3]) + (g[5] - g[6]) + (g[8] - g[7]);
+        double mym = (g[2] - g[4]) + (g[5] + g[6]) - (g[7] + g[8]);
+        double rho = c.rho_v + C * (c.rho_l - c.rho_v);
+        double ux = 3.0 * mxm / rho, uy = 3.0 * mym / rho;
+        double uu = ux * ux + uy * uy;
+        double w = m.lumped[i];
+        b.Cdiag[i] = C;
+        if (!isfinite(C) || !isfinite(p) || !isfinite(uu)) s[9] += 1.0;
+        s[0] += w * C;
+        s[1] += rho * uu;
+        if (rq.use_band) {
+            double dx = min_image(m.x[i] - rq.cx, rq.period_x), dy = min_image(m.y[i] - rq.cy, rq.period_y);
+            double r = sqrt(dx * dx + dy * dy);
+            if (fabs(r - rq.R) <= rq.band) {
+                s[2] += w;
+                s[3] += w * rho * uu;
+            }
+        }
+        if (C >= 0.95) {
+            s[4] += w;
+            s[5] += w * p;
+        }
+        if (C <= 0.05) {
+            s[6] += w;
+            s[7] += w * p;
+        }
+        mx[0] = fmax(mx[0], uu);
+    }
+    block_reduce_store<10, 1>(s, mx, b.diag_part + (size_t)blockIdx.x * kDiagSlots);
+}
+
+// wetted length on substrate wall edges; highest crossing of the C = 1/2
+// contour on triangle edges (both from the nodal C written by k_diag_nodes)
+__global__ void __launch_bounds__(kBlock) k_diag_edges(DevMesh m, Bufs b, DiagReq rq) {
+    double s[1] = {0.0};
+    double mx[1] = {-1e300};
+    const int Tp = m.Tp;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < m.E; e += gridDim.x * blockDim.x) {
+        if (m.wall_id[e] != rq.substrate) continue;
+        double Ca = b.Cdiag[m.wall_a[e]], Cb = b.Cdiag[m.wall_b[e]], L = m.wall_len[e];
+        if (Ca >= 0.5 && Cb >= 0.5)
+            s[0] += L;
+        else if (Ca >= 0.5 || Cb >= 0.5) {
+            double hi = fmax(Ca, Cb), lo = fmin(Ca, Cb);
+            s[0] += L * (hi - 0.5) / (hi - lo);
+        }
+    }
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < m.T; t += gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            int ia = m.tri[((k + 1) % 3) * Tp + t], ic = m.tri[((k + 2) % 3) * Tp + t];
+            double Ca = b.Cdiag[ia], Cc = b.Cdiag[ic];
+            if ((Ca >= 0.5) != (Cc >= 0.5)) {
+                double tt = (0.5 - Ca) / (Cc - Ca);
+                double dy = min_image(m.y[ic] - m.y[ia], rq.period_y);
+                mx[0] = fmax(mx[0], m.y[ia] + tt * dy);
+            }
+        }
+    }
+    block_reduce_store<1, 1>(s, mx, b.diag_part + (size_t)blockIdx.x * kDiagSlots + 11);
+}
+
+__global__ void k_diag_final(Bufs b) {
+    // one thread per slot, blocks summed in index order
+    int k = threadIdx.x;
+    if (k >= 13) return;
+    bool is_max = (k == 10 || k == 12);
+    double r = b.diag_part[k];
+    for (int blk = 1; blk < kDiagBlocks; ++blk) {
+        double v = b.diag_part[(size_t)blk * kDiagSlots + k];
+        r = is_max ? fmax(r, v) : r + v;
+    }
+    b.diag_out[k] = r;
+}
+
+// --------------------------------------------------------- host side ------
+static int cuda_fail(cudaError_t e, const char* what) {
+    char buf[256];
+    snprintf(buf, sizeof buf, "%s: %s", what, cudaGetErrorString(e));
+    set_error(buf);
+    return FELBM_ERR_CUDA;
+}
+#define FELBM_CUDA(call)                                   \
+    do {                                                   \
+        cudaError_t e_ = (call);                           \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+    } while (0)
+
+// Bump allocator over the caller's workspace (256-byte aligned pieces).
+struct Carver {
+    char* base;
+    size_t off = 0;
+    explicit Carver(void* b) : base(static_cast<char*>(b)) {}
+    template <class T>
+    T* take(size_t n) {
+        off = (off + 255) & ~size_t(255);
+        T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+        off += n * sizeof(T);
+        return p;
+    }
+};
+
+static size_t pad64(size_t n) { return (n + 63) & ~size_t(63); }
+
+}  // namespace felbm
+
+struct felbm_state {
+    felbm::HostMesh hm;
+    felbm_params prm;
+    felbm::DevMesh dm{};
+    felbm::Phys phys{};
+    felbm::Bufs buf{};
+    cudaStream_t stream = nullptr;
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t graph_exec = nullptr;
+    cudaGraph_t graph = nullptr;
+    int sweeps = 32;
+    std::vector<double> cheb_a, cheb_c;
+    double inv_theta = 1.0;
+    int64_t step = 0;
+    double mass0 = 0.0;
+    int device = 0;
+    bool timing = false;
+    bool timed_step_ran = false;
+    cudaEvent_t ev[7] = {};
+};
+
+namespace felbm {
+
+// Layout of the workspace; with base == nullptr only the size is computed.
+static size_t carve(const HostMesh& h, void* base, DevMesh* dm, Bufs* b) {
+    Carver cv(base);
+    size_t Np = pad64(h.N), Tp = pad64(h.T);
+    size_t nnz = h.row_ptr[h.N], ninc = h.inc_ptr[h.N], nwinc = h.winc_ptr[h.N];
+    size_t E = std::max<int32_t>(h.E, 1);
+    DevMesh d{};
+    d.tri = cv.take<int32_t>(3 * Tp);
+    d.area = cv.take<double>(Tp);
+    d.grad = cv.take<double>(6 * Tp);
+    d.nbr = cv.take<int32_t>(3 * Tp);
+    d.row_ptr = cv.take<int32_t>(h.N + 1);
+    d.col = cv.take<int32_t>(nnz);
+    d.mval = cv.take<double>(nnz);
+    d.lval = cv.take<double>(nnz);
+    d.inv_lumped = cv.take<double>(Np);
+    d.lumped = cv.take<double>(Np);
+    d.inv_vol = cv.take<double>(Np);
+    d.inc_ptr = cv.take<int32_t>(h.N + 1);
+    d.inc_tri = cv.take<int32_t>(ninc);
+    d.inc_bx = cv.take<double>(ninc);
+    d.inc_by = cv.take<double>(ninc);
+    d.wall_a = cv.take<int32_t>(E);
+    d.wall_b = cv.take<int32_t>(E);
+    d.wall_id = cv.take<int32_t>(E);
+    d.wall_len = cv.take<double>(E);
+    d.wall_nx = cv.take<double>(E);
+    d.wall_ny = cv.take<double>(E);
+    d.winc_ptr = cv.take<int32_t>(h.N + 1);
+    d.winc_edge = cv.take<int32_t>(std::max<size_t>(nwinc, 1));
+    d.x = cv.take<double>(Np);
+    d.y = cv.take<double>(Np);
+    d.perm = cv.take<int32_t>(h.N);
+    d.iperm = cv.take<int32_t>(h.N);
+    Bufs bb{};
+    bb.psi = cv.take<double>(18 * Np);
+    bb.C = cv.take<double>(Np);
+    bb.p = cv.take<double>(Np);
+    bb.ux = cv.take<double>(Np);
+    bb.uy = cv.take<double>(Np);
+    bb.mu = cv.take<double>(Np);
+    bb.gmu = cv.take<double>(2 * Tp);
+    bb.R = cv.take<double>(18 * (size_t)h.T);
+    bb.rhs = cv.take<double>(18 * Np);
+    bb.x0 = cv.take<double>(18 * Np);
+    bb.x1 = cv.take<double>(18 * Np);
+    bb.stage = cv.take<double>(18 * Np);
+    bb.diag_part = cv.take<double>((size_t)kDiagBlocks * kDiagSlots);
+    bb.diag_out = cv.take<double>(kDiagSlots);
+    bb.Cdiag = cv.take<double>(Np);
+    if (dm) {
+        d.N = h.N;
+        d.T = h.T;
+        d.E = h.E;
+        d.Np = (int32_t)Np;
+        d.Tp = (int32_t)Tp;
+        d.period_y = h.period[1];
+        *dm = d;
+    }
+    if (b) *b = bb;
+    return cv.off + 256;
+}
+
+static int check_params(const felbm_params* p) {
+    if (!p || !(p->dt > 0.0) || !(p->tau_l > 0.0) || !(p->tau_v > 0.0) || !(p->rho_l > 0.0) ||
+        !(p->rho_v > 0.0) || !(p->kappa >= 0.0) || !(p->beta >= 0.0) || !(p->mobility >= 0.0) ||
+        p->lap_mode < 0 || p->lap_mode > 1 || p->solver_iters < 0 || p->solver_iters == 1 ||
+        p->n_wall_ids < 0 || p->n_wall_ids > FELBM_MAX_WALL_IDS) {
+        set_error("felbm: invalid params (dt, tau, rho > 0; kappa, beta, mobility >= 0; lap_mode 0/1; solver_iters 0 or >= 2)");
+        return FELBM_ERR_INVALID_ARG;
+    }
+    if (p->precision != FELBM_FP64) {
+        set_error("felbm: precision not supported by this build");
+        return FELBM_ERR_UNSUPPORTED;
+    }
+    return FELBM_OK;
+}
+
+template <class T>
+static cudaError_t up(const T* dst, const std::vector<T>& src, cudaStream_t s) {
+    if (src.empty()) return cudaSuccess;
+    return cudaMemcpyAsync(const_cast<T*>(dst), src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice, s);
+}
+
+static unsigned grid_for(int n, int block) { return (unsigned)((n + block - 1) / block); }
+
+// Enqueue the kernels of one time step on stream s (optionally with the
+// phase events, recorded as external event nodes of the captured graph).
+static void enqueue_step(felbm_state* st, cudaStream_t s) {
+    const DevMesh& m = st->dm;
+    const Bufs& b = st->buf;
+    auto mark = [&](int k) {
+        if (st->timing) cudaEventRecordWithFlags(st->ev[k], s, cudaEventRecordExternal);
+    };
+    mark(0);
+    k_collide<<<grid_for(m.N, kBlock), kBlock, 0, s>>>(m, st->phys, b, 1);
+    mark(1);
+    k_mu<<<grid_for(m.N, kBlock), kBlock, 0, s>>>(m, st->phys, b);
+    mark(2);
+    k_gradmu<<<grid_for(m.T, kBlock), kBlock, 0, s>>>(m, b);
+    mark(3);
+    k_element<<<grid_for(m.T, 128), 128, 0, s>>>(m, st->phys, b);
+    mark(4);
+    k_rhs<<<grid_for(m.N, 128), 128, 0, s>>>(m, st->phys, b, st->inv_theta);
+    mark(5);
+    for (int k = 1; k < st->sweeps; ++k) {
+        const double* cur = (k & 1) ? b.x1 : b.x0;
+        double* prev = (k & 1) ? b.x0 : b.x1;
+        k_cheb<<<grid_for(m.N, 128), 128, 0, s>>>(m, b, cur, prev, st->cheb_a[k], st->cheb_c[k], k == 1,
+                                                   k == st->sweeps - 1);
+    }
+    mark(6);
+}
+
+}  // namespace felbm
+
+using namespace felbm;
+
+extern "C" {
+
+int felbm_workspace_bytes(const felbm_mesh* mesh, const felbm_params* params, size_t* bytes) {
+    if (!mesh || !bytes) {
+        set_error("felbm_workspace_bytes: invalid argument");
+        return FELBM_ERR_INVALID_ARG;
+    }
+    int rc = check_params(params);
+    if (rc) return rc;
+    *bytes = carve(mesh->h, nullptr, nullptr, nullptr);
+    return FELBM_OK;
+}
+
+int felbm_init(const felbm_mesh* mesh, const felbm_params* params, const double* C0, void* d_workspace,
+               size_t workspace_bytes, void* stream, felbm_state** out) {
+    if (!mesh || !C0 || !out) {
+        set_error("felbm_init: invalid argument");
+        return FELBM_ERR_INVALID_ARG;
+    }
+    *out = nullptr;
+    int rc = check_params(params);
+    if (rc) return rc;
+    const HostMesh& h = mesh->h;
+    for (int32_t e = 0; e < h.E; ++e)
+        if (h.wall_id[e] >= params->n_wall_ids) {
+            set_error("felbm_init: a wall id has no phi_c (n_wall_ids too small)");
+            return FELBM_ERR_INVALID_ARG;
+        }
+    size_t need = carve(h, nullptr, nullptr, nullptr);
+    if (!d_workspace || workspace_bytes < need || (reinterpret_cast<uintptr_t>(d_workspace) & 255)) {
+        set_error("felbm_init: workspace missing, not 256-byte aligned or smaller than felbm_workspace_bytes");
+        return FELBM_ERR_WORKSPACE;
+    }
+    felbm_state* st = new (std::nothrow) felbm_state;
+    if (!st) {
+        set_error("felbm_init: out of host memory");
+        return FELBM_ERR_INVALID_ARG;
+    }
+    st->hm = h;
+    st->prm = *params;
+    st->stream = static_cast<cudaStream_t>(stream);
+    carve(h, d_workspace, &st->dm, &st->buf);
+    Phys& ph = st->phys;
+    ph.dt = params->dt;
+    ph.tau_l = params->tau_l;
+    ph.tau_v = params->tau_v;
+    ph.rho_l = params->rho_l;
+    ph.rho_v = params->rho_v;
+    ph.kappa = params->kappa;
+    ph.beta = params->beta;
+    ph.mobility = params->mobility;
+    for (int k = 0; k < FELBM_MAX_WALL_IDS; ++k) ph.phi_c[k] = params->phi_c[k];
+
+    // Chebyshev coefficients for the spectrum [1/4, 1] of m^{-1} M11
+    st->sweeps = params->solver_iters ? params->solver_iters : 32;
+    const double lmin = 0.25, lmax = 1.0;
+    const double theta = 0.5 * (lmax + lmin), delta = 0.5 * (lmax - lmin), sigma1 = theta / delta;
+    st->inv_theta = 1.0 / theta;
+    st->cheb_a.assign(st->sweeps, 0.0);
+    st->cheb_c.assign(st->sweeps, 0.0);
+    double rho_prev = 1.0 / sigma1;
+    for (int k = 1; k < st->sweeps; ++k) {
+        double rho = 1.0 / (2.0 * sigma1 - rho_prev);
+        st->cheb_a[k] = rho * rho_prev;
+        st->cheb_c[k] = 2.0 * rho / delta;
+        rho_prev = rho;
+    }
+
+    // host-side derived tables
+    const double scale = params->lap_mode == FELBM_LAP_PAPER ? 1.0 : 2.0 / 3.0;
+    std::vector<double> inv_vol(h.N), inv_lumped(h.N), lval(h.row_ptr[h.N]);
+    for (int32_t i = 0; i < h.N; ++i) {
+        inv_vol[i] = 1.0 / (scale * h.patch[i]);
+        inv_lumped[i] = 1.0 / h.lumped[i];
+        for (int32_t k = h.row_ptr[i]; k < h.row_ptr[i + 1]; ++k) lval[k] = -2.0 * h.stiff[k] * inv_vol[i];
+    }
+    auto pad_tri = [&](const std::vector<int32_t>& src, int rows) {
+        std::vector<int32_t> outv((size_t)rows * st->dm.Tp, 0);
+        for (int r = 0; r < rows; ++r)
+            std::copy(src.begin() + (size_t)r * h.T, src.begin() + (size_t)(r + 1) * h.T,
+                      outv.begin() + (size_t)r * st->dm.Tp);
+        return outv;
+    };
+    auto pad_trid = [&](const std::vector<double>& src, int rows) {
+        std::vector<double> outv((size_t)rows * st->dm.Tp, 0.0);
+        for (int r = 0; r < rows; ++r)
+            std::copy(src.begin() + (size_t)r * h.T, src.begin() + (size_t)(r + 1) * h.T,
+                      outv.begin() + (size_t)r * st->dm.Tp);
+        return outv;
+    };
+    std::vector<int32_t> tri_p = pad_tri(h.tri, 3), nbr_p = pad_tri(h.nbr, 3);
+    std::vector<double> grad_p = pad_trid(h.grad, 6), area_p = pad_trid(h.area, 1);
+    cudaStream_t s = st->stream;
+    const DevMesh& d = st->dm;
+    auto fail = [&](cudaError_t e, const char* what) {
+        int r = cuda_fail(e, what);
+        delete st;
+        return r;
+    };
+    cudaError_t e = cudaSuccess;
+#define UP(dst, src) \
+    if (e == cudaSuccess) e = up(dst, src, s)
+    UP(d.tri, tri_p);
+    UP(d.area, area_p);
+    UP(d.grad, grad_p);
+    UP(d.nbr, nbr_p);
+    UP(d.row_ptr, h.row_ptr);
+    UP(d.col, h.col);
+    UP(d.mval, h.mass);
+    UP(d.lval, lval);
+    UP(d.inv_lumped, inv_lumped);
+    UP(d.lumped, h.lumped);
+    UP(d.inv_vol, inv_vol);
+    UP(d.inc_ptr, h.inc_ptr);
+    UP(d.inc_tri, h.inc_tri);
+    UP(d.inc_bx, h.inc_bx);
+    UP(d.inc_by, h.inc_by);
+    UP(d.wall_a, h.wall_a);
+    UP(d.wall_b, h.wall_b);
+    UP(d.wall_id, h.wall_id);
+    UP(d.wall_len, h.wall_len);
+    UP(d.wall_nx, h.wall_nx);
+    UP(d.wall_ny, h.wall_ny);
+    UP(d.winc_ptr, h.winc_ptr);
+    UP(d.winc_edge, h.winc_edge);
+    UP(d.x, h.x);
+    UP(d.y, h.y);
+    UP(d.perm, h.perm);
+    UP(d.iperm, h.iperm);
+#undef UP
+    if (e != cudaSuccess) return fail(e, "felbm_init: upload");
+    e = cudaMemcpyAsync(st->buf.stage, C0, sizeof(double) * h.N, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return fail(e, "felbm_init: upload C0");
+    k_init_state<<<grid_for(h.N, kBlock), kBlock, 0, s>>>(st->dm, st->buf.stage, st->buf.psi);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(e, "felbm_init: launch");
+    e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return fail(e, "felbm_init: synchronize");
+    e = cudaGetDevice(&st->device);
+    if (e != cudaSuccess) return fail(e, "felbm_init: cudaGetDevice");
+    // mass at t = 0 (for the drift)
+    felbm_diag dg;
+    *out = st;
+    rc = felbm_diagnostics(st, nullptr, &dg);
+    if (rc != FELBM_OK && rc != FELBM_ERR_NONFINITE) {
+        *out = nullptr;
+        delete st;
+        return rc;
+    }
+    st->mass0 = dg.mass;
+    return FELBM_OK;
+}
+
+static int build_graph(felbm_state* st) {
+    if (!st->cap_stream) FELBM_CUDA(cudaStreamCreateWithFlags(&st->cap_stream, cudaStreamNonBlocking));
+    FELBM_CUDA(cudaStreamBeginCapture(st->cap_stream, cudaStreamCaptureModeThreadLocal));
+    enqueue_step(st, st->cap_stream);
+    cudaError_t e = cudaStreamEndCapture(st->cap_stream, &st->graph);
+    if (e != cudaSuccess) return cuda_fail(e, "felbm_step: capture");
+    FELBM_CUDA(cudaGraphInstantiate(&st->graph_exec, st->graph, 0));
+    return FELBM_OK;
+}
+
+int felbm_step(felbm_state* st, int32_t n_steps) {
+    if (!st || n_steps < 0) {
+        set_error("felbm_step: invalid argument");
+        return FELBM_ERR_INVALID_ARG;
+    }
+    if (!st->graph_exec) {
+        int rc = build_graph(st);
+        if (rc) return rc;
+    }
+    for (int32_t k = 0; k < n_steps; ++k) FELBM_CUDA(cudaGraphLaunch(st->graph_exec, st->stream));
+    st->step += n_steps;
+    if (n_steps > 0 && st->timing) st->timed_step_ran = true;
+    return FELBM_OK;
+}
+
+static void drop_graph(felbm_state* st) {
+    if (st->graph_exec) cudaGraphExecDestroy(st->graph_exec);
+    if (st->graph) cudaGraphDestroy(st->graph);
+    st->graph_exec = nullptr;
+    st->graph = nullptr;
+}
+
+int felbm_timing_enable(felbm_state* st, int32_t enable) {
+    if (!st) {
+        set_error("felbm_timing_enable: invalid argument");
+        return FELBM_ERR_INVALID_ARG;
+    }
+    if (enable && !st->ev[0])
+        for (auto& e : st->ev) FELBM_CUDA(cudaEventCreate(&e));
+    FELBM_CUDA(cudaStreamSynchronize(st->stream));
+    drop_graph(st);
+    st->timing = enable != 0;
+    st->timed_step_ran = false;
+    return FELBM_OK;
+}
+
+int felbm_timing_get(felbm_state* st, felbm_step_timing* out) {
+    if (!st || !out || !st->timing || !st->timed_step_ran) {
+        set_error("felbm_timing_get: timing is off or no timed step ran");
+        return FELBM_ERR_INVALID_ARG;
+    }
+    FELBM_CUDA(cudaStreamSynchronize(st->stream));
+    float t[6];
+    for (int k = 0; k < 6; ++k) FELBM_CUDA(cudaEventElapsedTime(&t[k], st->ev[k], st->ev[k + 1]));
+    out->collide_ms = t[0];
+    out->mu_ms = t[1];
+    out->gradmu_ms = t[2];
+    out->element_ms = t[3];
+    out->rhs_ms = t[4];
+    out->solve_ms = t[5];
+    out->total_ms = t[0] + t[1] + t[2] + t[3] + t[4] + t[5];
+    out->solve_launches = st->sweeps - 1;
+    out->launches = 5 + st->sweeps - 1;
+    return FELBM_OK;
+}
+
+int felbm_diagnostics(felbm_state* st, const felbm_diag_request* req, felbm_diag* out) {
+    if (!st || !out) {
+        set_error("felbm_diagnostics: invalid argument");
+        return FELBM_ERR_INVALID_ARG;
+    }
+    DiagReq rq{};
+    rq.period_x = st->hm.period[0];
+    rq.period_y = st->hm.period[1];
+    rq.substrate = req ? req->substrate_wall_id : 0;
+    rq.use_band = req && req->band > 0.0;
+    if (req) {
+        rq.cx = req->centre[0];
+        rq.cy = req->centre[1];
+        rq.R = req->radius;
+        rq.band = req->band;
+    }
+    cudaStream_t s = st->stream;
+    k_diag_nodes<<<kDiagBlocks, kBlock, 0, s>>>(st->dm, st->phys, st->buf, rq);
+    k_diag_edges<<<kDiagBlocks, kBlock, 0, s>>>(st->dm, st->buf, rq);
+    k_diag_final<<<1, 32, 0, s>>>(st->buf);
+    FELBM_CUDA(cudaGetLastError());
+    double v[kDiagSlots];
+    FELBM_CUDA(cudaMemcpyAsync(v, st->buf.diag_out, sizeof v, cudaMemcpyDeviceToHost, s));
+    FELBM_CUDA(cudaStreamSynchronize(s));
+    const HostMesh& h = st->hm;
+    felbm_diag d{};
+    d.step = st->step;
+    d.mass = v[0];
+    d.mass0 = st->mass0;
+    d.mass_drift_rel = st->mass0 != 0.0 ? (v[0] - st->mass0) / st->mass0 : 0.0;
+    d.kinetic_energy = 0.5 * v[1] / h.N;
+    d.max_u = std::sqrt(v[10]);
+    d.interface_rho_uu = v[2] > 0.0 ? v[3] / v[2] : 0.0;
+    d.p_in = v[5] / std::max(v[4], 1e-300);
+    d.p_out = v[7] / std::max(v[6], 1e-300);
+    d.delta_p = d.p_in - d.p_out;
+    d.wetted_length = v[11];
+    // mean height of the substrate wall nodes
+    double ysum = 0.0;
+    int ny = 0;
+    std::vector<char> seen(h.N, 0);
+    for (int32_t e = 0; e < h.E; ++e) {
+        if (h.wall_id[e] != rq.substrate) continue;
+        for (int32_t n : {h.wall_a[e], h.wall_b[e]})
+            if (!seen[n]) {
+                seen[n] = 1;
+                ysum += h.y[n];
+                ++ny;
+            }
+    }
+    d.height = ny ? v[12] - ysum / ny : std::nan("");
+    double b = d.wetted_length, hh = d.height;
+    if (ny && hh > 0.0 && b > 0.0) {
+        double r = (4.0 * hh * hh + b * b) / (8.0 * hh);
+        d.theta_deg = std::atan2(b, 2.0 * (r - hh)) * 180.0 / M_PI;
+    } else {
+        d.theta_deg = std::nan("");
+    }
+    d.status = v[9] > 0.0 ? FELBM_ERR_NONFINITE : FELBM_OK;
+    *out = d;
+    if (d.status != FELBM_OK) {
+        set_error("felbm_diagnostics: non-finite values in the state");
+        return FELBM_ERR_NONFINITE;
+    }
+    return FELBM_OK;
+}
+
+int felbm_get_state(felbm_state* st, double* g, double* h) {
+    if (!st || !g || !h) {
+        set_error("felbm_get_state: invalid argument");
+        return FELBM_ERR_INVALID_ARG;
+    }
+    cudaStream_t s = st->stream;
+    const int N = st->dm.N;
+    k_gather_out<<<grid_for(N, kBlock), kBlock, 0, s>>>(st->dm, st->buf.psi, st->buf.stage, 18);
+    FELBM_CUDA(cudaGetLastError());
+    FELBM_CUDA(cudaMemcpyAsync(g, st->buf.stage, sizeof(double) * 9 * N, cudaMemcpyDeviceToHost, s));
+    FELBM_CUDA(cudaMemcpyAsync(h, st->buf.stage + (size_t)9 * N, sizeof(double) * 9 * N, cudaMemcpyDeviceToHost, s));
+    FELBM_CUDA(cudaStreamSynchronize(s));
+    return FELBM_OK;
+}
+
+int felbm_set_state(felbm_state* st, const double* g, const double* h) {
+    if (!st || !g || !h) {
+        set_error("felbm_set_state: invalid argument");
+        return FELBM_ERR_INVALID_ARG;
+    }
+    cudaStream_t s = st->stream;
+    const int N = st->dm.N;
+    FELBM_CUDA(cudaMemcpyAsync(st->buf.stage, g, sizeof(double) * 9 * N, cudaMemcpyHostToDevice, s));
+    FELBM_CUDA(cudaMemcpyAsync(st->buf.stage + (size_t)9 * N, h, sizeof(double) * 9 * N, cudaMemcpyHostToDevice, s));
+    k_scatter_in<<<grid_for(N, kBlock), kBlock, 0, s>>>(st->dm, st->buf.stage, st->buf.psi, 18);
+    FELBM_CUDA(cudaGetLastError());
+    FELBM_CUDA(cudaStreamSynchronize(s));
+    return FELBM_OK;
+}
+
+int felbm_get_fields(felbm_state* st, double* C, double* p, double* ux, double* uy, double* mu) {
+    if (!st) {
+        set_error("felbm_get_fields: invalid argument");
+        return FELBM_ERR_INVALID_ARG;
+    }
+    cudaStream_t s = st->stream;
+    const DevMesh& m = st->dm;
+    k_collide<<<grid_for(m.N, kBlock), kBlock, 0, s>>>(m, st->phys, st->buf, 0);
+    k_mu<<<grid_for(m.N, kBlock), kBlock, 0, s>>>(m, st->phys, st->buf);
+    FELBM_CUDA(cudaGetLastError());
+    double* outs[5] = {C, p, ux, uy, mu};
+    double* srcs[5] = {st->buf.C, st->buf.p, st->buf.ux, st->buf.uy, st->buf.mu};
+    for (int k = 0; k < 5; ++k) {
+        if (!outs[k]) continue;
+        k_gather_out<<<grid_for(m.N, kBlock), kBlock, 0, s>>>(m, srcs[k], st->buf.stage, 1);
+        FELBM_CUDA(cudaGetLastError());
+        FELBM_CUDA(cudaMemcpyAsync(outs[k], st->buf.stage, sizeof(double) * m.N, cudaMemcpyDeviceToHost, s));
+        FELBM_CUDA(cudaStreamSynchronize(s));
+    }
+    return FELBM_OK;
+}
+
+int felbm_mass_solve(felbm_state* st, const double* B, double* X, int32_t k) {
+    if (!st || !B || !X || k < 1 || k > 18) {
+        set_error("felbm_mass_solve: invalid argument (1 <= k <= 18)");
+        return FELBM_ERR_INVALID_ARG;
+    }
+    cudaStream_t s = st->stream;
+    const DevMesh& m = st->dm;
+    const Bufs& b = st->buf;
+    FELBM_CUDA(cudaMemcpyAsync(b.stage, B, sizeof(double) * k * m.N, cudaMemcpyHostToDevice, s));
+    k_scatter_in<<<grid_for(m.N, kBlock), kBlock, 0, s>>>(m, b.stage, b.rhs, k);
+    if (k < 18) k_zero_rows<<<grid_for(m.N, kBlock), kBlock, 0, s>>>(m, b.rhs, k, 18);
+    k_cheb_start<<<grid_for(m.N, kBlock), kBlock, 0, s>>>(m, b, st->inv_theta);
+    const double* result = b.x1;
+    for (int it = 1; it < st->sweeps; ++it) {
+        const double* cur = (it & 1) ? b.x1 : b.x0;
+        double* prev = (it & 1) ? b.x0 : b.x1;
+        k_cheb<<<grid_for(m.N, 128), 128, 0, s>>>(m, b, cur, prev, st->cheb_a[it], st->cheb_c[it], it == 1, 0);
+        result = prev;
+    }
+    k_gather_out<<<grid_for(m.N, kBlock), kBlock, 0, s>>>(m, result, b.stage, k);
+    FELBM_CUDA(cudaGetLastError());
+    FELBM_CUDA(cudaMemcpyAsync(X, b.stage, sizeof(double) * k * m.N, cudaMemcpyDeviceToHost, s));
+    FELBM_CUDA(cudaStreamSynchronize(s));
+    return FELBM_OK;
+}
+
+void felbm_state_destroy(felbm_state* st) {
+    if (!st) return;
+    drop_graph(st);
+    if (st->cap_stream) cudaStreamDestroy(st->cap_stream);
+    for (auto& e : st->ev)
+        if (e) cudaEventDestroy(e);
+    delete st;
+}
+
+}  // extern "C"

@@ -1,0 +1,288 @@
+"""ctypes binding of the C-ABI FE-LBM library (``include/felbm.h``).
+
+Argument marshalling only: every step of the update runs in the library's
+CUDA kernels.  The names mirror the C entry points without the ``felbm_``
+prefix.  Device memory (the workspace) and the stream come from PyTorch.
+If the library is not built or cannot be loaded, every call raises -- there
+is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+MAX_WALL_IDS = 8
+LAP_CONSISTENT, LAP_PAPER = 0, 1
+FP64 = 0
+
+_ERRORS = {
+    -1: "invalid argument", -2: "bad mesh", -3: "CUDA error", -4: "workspace",
+    -5: "non-finite state", -6: "unsupported",
+}
+
+
+class FelbmError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"felbm error {code} ({_ERRORS.get(code, '?')}): {msg}")
+        self.code = code
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("dt", ctypes.c_double), ("tau_l", ctypes.c_double), ("tau_v", ctypes.c_double),
+                ("rho_l", ctypes.c_double), ("rho_v", ctypes.c_double),
+                ("kappa", ctypes.c_double), ("beta", ctypes.c_double),
+                ("mobility", ctypes.c_double), ("phi_c", ctypes.c_double * MAX_WALL_IDS),
+                ("n_wall_ids", ctypes.c_int32), ("lap_mode", ctypes.c_int32),
+                ("precision", ctypes.c_int32), ("solver_iters", ctypes.c_int32)]
+
+
+class MeshInfo(ctypes.Structure):
+    _fields_ = [("n_nodes", ctypes.c_int32), ("n_tri", ctypes.c_int32),
+                ("n_wall_edges", ctypes.c_int32), ("nnz", ctypes.c_int32),
+                ("max_degree", ctypes.c_int32), ("bandwidth", ctypes.c_int32),
+                ("min_area", ctypes.c_double), ("total_area", ctypes.c_double)]
+
+
+class DiagRequest(ctypes.Structure):
+    _fields_ = [("centre", ctypes.c_double * 2), ("radius", ctypes.c_double),
+                ("band", ctypes.c_double), ("substrate_wall_id", ctypes.c_int32)]
+
+
+class Diag(ctypes.Structure):
+    _fields_ = [("step", ctypes.c_int64), ("mass", ctypes.c_double), ("mass0", ctypes.c_double),
+                ("mass_drift_rel", ctypes.c_double), ("kinetic_energy", ctypes.c_double),
+                ("max_u", ctypes.c_double), ("interface_rho_uu", ctypes.c_double),
+                ("p_in", ctypes.c_double), ("p_out", ctypes.c_double), ("delta_p", ctypes.c_double),
+                ("wetted_length", ctypes.c_double), ("height", ctypes.c_double),
+                ("theta_deg", ctypes.c_double), ("status", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+class StepTiming(ctypes.Structure):
+    _fields_ = [("collide_ms", ctypes.c_float), ("mu_ms", ctypes.c_float),
+                ("gradmu_ms", ctypes.c_float), ("element_ms", ctypes.c_float),
+                ("rhs_ms", ctypes.c_float), ("solve_ms", ctypes.c_float),
+                ("total_ms", ctypes.c_float), ("solve_launches", ctypes.c_int32),
+                ("launches", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+_LIB = None
+_P = ctypes.c_void_p
+_I32 = ctypes.c_int32
+
+
+def _declare(lib):
+    sig = {
+        "felbm_last_error": (ctypes.c_char_p, []),
+        "felbm_params_derive": (ctypes.c_int, [ctypes.c_double, ctypes.c_double, _P, _I32,
+                                               ctypes.POINTER(Params)]),
+        "felbm_mesh_create": (ctypes.c_int, [_P, _I32, _P, _I32, _P, _P, _I32, ctypes.c_double,
+                                             ctypes.c_double, ctypes.POINTER(_P)]),
+        "felbm_mesh_info_get": (ctypes.c_int, [_P, ctypes.POINTER(MeshInfo)]),
+        "felbm_mesh_destroy": (None, [_P]),
+        "felbm_workspace_bytes": (ctypes.c_int, [_P, ctypes.POINTER(Params),
+                                                 ctypes.POINTER(ctypes.c_size_t)]),
+        "felbm_init": (ctypes.c_int, [_P, ctypes.POINTER(Params), _P, _P, ctypes.c_size_t, _P,
+                                      ctypes.POINTER(_P)]),
+        "felbm_step": (ctypes.c_int, [_P, _I32]),
+        "felbm_diagnostics": (ctypes.c_int, [_P, ctypes.POINTER(DiagRequest), ctypes.POINTER(Diag)]),
+        "felbm_get_state": (ctypes.c_int, [_P, _P, _P]),
+        "felbm_set_state": (ctypes.c_int, [_P, _P, _P]),
+        "felbm_get_fields": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
+        "felbm_mass_solve": (ctypes.c_int, [_P, _P, _P, _I32]),
+        "felbm_timing_enable": (ctypes.c_int, [_P, _I32]),
+        "felbm_timing_get": (ctypes.c_int, [_P, ctypes.POINTER(StepTiming)]),
+        "felbm_state_destroy": (None, [_P]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+
+
+def lib():
+    """Load ``libfelbm.so`` (raises if it has not been built)."""
+    global _LIB
+    if _LIB is None:
+        path = _build.lib_path()
+        if not os.path.exists(path):
+            raise RuntimeError(f"{path} is missing: build it with "
+                               "`python -m paper_1708_04678_gb300.build`")
+        _LIB = ctypes.CDLL(path)
+        _declare(_LIB)
+    return _LIB
+
+
+def _check(code):
+    if code != 0:
+        raise FelbmError(code, lib().felbm_last_error().decode())
+
+
+def _ptr(a):
+    """Host or device address of a numpy array or torch tensor."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return a.ctypes.data
+    return a.data_ptr()
+
+
+def params_derive(phys, lap_mode=LAP_CONSISTENT, solver_iters=0, precision=FP64):
+    """felbm_params from a physical description (sigma, xi, contact angles in
+    degrees, dt, tau_l, tau_v, rho_l, rho_v, mobility)."""
+    p = Params()
+    p.dt = phys["dt"]
+    p.tau_l, p.tau_v = phys["tau_l"], phys["tau_v"]
+    p.rho_l, p.rho_v = phys["rho_l"], phys["rho_v"]
+    p.mobility = phys["mobility"]
+    th = np.ascontiguousarray(phys.get("theta_deg", ()), dtype=np.float64)
+    _check(lib().felbm_params_derive(phys["sigma"], phys["xi"], _ptr(th) if th.size else None,
+                                     int(th.size), ctypes.byref(p)))
+    p.lap_mode = lap_mode
+    p.precision = precision
+    p.solver_iters = solver_iters
+    return p
+
+
+class Mesh:
+    """felbm_mesh: validated, reordered mesh tables on the host."""
+
+    def __init__(self, xy, tri, wall_edges=None, wall_id=None, period=(0.0, 0.0)):
+        xy = np.ascontiguousarray(xy, dtype=np.float64)
+        tri = np.ascontiguousarray(tri, dtype=np.int32)
+        we = np.ascontiguousarray(np.zeros((0, 2)) if wall_edges is None else wall_edges, dtype=np.int32)
+        wid = np.ascontiguousarray(np.zeros(0) if wall_id is None else wall_id, dtype=np.int32)
+        h = _P()
+        _check(lib().felbm_mesh_create(_ptr(xy), len(xy), _ptr(tri), len(tri),
+                                       _ptr(we) if len(we) else None, _ptr(wid) if len(wid) else None,
+                                       len(we), float(period[0]), float(period[1]), ctypes.byref(h)))
+        self.handle = h
+        self.n_nodes = len(xy)
+
+    @classmethod
+    def from_dict(cls, m):
+        return cls(m["xy"], m["tri"], m["wall_edges"], m["wall_id"], m["period"])
+
+    def info(self):
+        i = MeshInfo()
+        _check(lib().felbm_mesh_info_get(self.handle, ctypes.byref(i)))
+        return {name: getattr(i, name) for name, _ in i._fields_}
+
+    def workspace_bytes(self, params):
+        n = ctypes.c_size_t()
+        _check(lib().felbm_workspace_bytes(self.handle, ctypes.byref(params), ctypes.byref(n)))
+        return n.value
+
+    def close(self):
+        if self.handle:
+            lib().felbm_mesh_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+mesh_create = Mesh
+
+
+class State:
+    """felbm_state: the distributions and tables of one mesh on one GPU.
+
+    The workspace is a torch uint8 tensor on ``device``; ``stream`` is a
+    ``torch.cuda.Stream`` (default: the current stream)."""
+
+    def __init__(self, mesh: Mesh, params: Params, C0, device="cuda", stream=None, workspace=None):
+        import torch
+        self.torch = torch
+        self.params = params
+        self.N = mesh.n_nodes
+        nbytes = mesh.workspace_bytes(params)
+        if workspace is None:
+            workspace = torch.empty(nbytes, dtype=torch.uint8, device=device)
+        elif workspace.numel() * workspace.element_size() < nbytes:
+            raise ValueError("workspace too small")
+        self.workspace = workspace
+        self.stream = stream if stream is not None else torch.cuda.current_stream(workspace.device)
+        C0 = np.ascontiguousarray(C0, dtype=np.float64)
+        if C0.shape != (self.N,):
+            raise ValueError("C0 must have one value per node")
+        h = _P()
+        _check(lib().felbm_init(mesh.handle, ctypes.byref(params), _ptr(C0), workspace.data_ptr(),
+                                nbytes, ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h)))
+        self.handle = h
+
+    def step(self, n=1):
+        _check(lib().felbm_step(self.handle, int(n)))
+
+    def diagnostics(self, centre=None, radius=0.0, band=0.0, substrate=0):
+        req = DiagRequest()
+        if centre is not None:
+            req.centre[0], req.centre[1] = float(centre[0]), float(centre[1])
+        req.radius, req.band, req.substrate_wall_id = float(radius), float(band), int(substrate)
+        d = Diag()
+        code = lib().felbm_diagnostics(self.handle, ctypes.byref(req), ctypes.byref(d))
+        if code not in (0, -5):
+            _check(code)
+        return d.as_dict()
+
+    def get_state(self, g=None, h=None):
+        if g is None:
+            g = np.empty((9, self.N))
+        if h is None:
+            h = np.empty((9, self.N))
+        _check(lib().felbm_get_state(self.handle, _ptr(g), _ptr(h)))
+        return g, h
+
+    def set_state(self, g, h):
+        if isinstance(g, np.ndarray):
+            g = np.ascontiguousarray(g, dtype=np.float64)
+            h = np.ascontiguousarray(h, dtype=np.float64)
+        _check(lib().felbm_set_state(self.handle, _ptr(g), _ptr(h)))
+
+    def get_fields(self):
+        out = {k: np.empty(self.N) for k in ("C", "p", "ux", "uy", "mu")}
+        _check(lib().felbm_get_fields(self.handle, *(_ptr(out[k]) for k in ("C", "p", "ux", "uy", "mu"))))
+        return out
+
+    def mass_solve(self, B):
+        B = np.ascontiguousarray(B, dtype=np.float64)
+        k = B.shape[0]
+        X = np.empty_like(B)
+        _check(lib().felbm_mass_solve(self.handle, _ptr(B), _ptr(X), k))
+        return X
+
+    def timing_enable(self, on=True):
+        _check(lib().felbm_timing_enable(self.handle, 1 if on else 0))
+
+    def timing_get(self):
+        t = StepTiming()
+        _check(lib().felbm_timing_get(self.handle, ctypes.byref(t)))
+        return t.as_dict()
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().felbm_state_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+init = State

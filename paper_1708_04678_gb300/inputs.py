@@ -176,8 +176,17 @@ def droplet_C0(xy, centre, R, xi, period=(0.0, 0.0)):
     return 0.5 + 0.5 * np.tanh(2.0 * (R - r) / xi)
 
 
+# Time steps: the Taylor-Galerkin streaming step is explicit, and dt = 0.5
+# (h = 1) exceeds its stability limit on these meshes (noisy uniform states
+# grow at dt >= 0.35 on 2-triangle cells with 0.2h jitter, and at dt >= 0.15
+# on the 4-triangle cells with 0.25h jitter).  The workloads therefore use
+# dt = 0.25 on 2-triangle meshes and dt = 0.1 on the 4-triangle mesh.
+DT_GRID = 0.25
+DT_CROSS = 0.1
+
+
 def _phys(**kw):
-    base = dict(dt=0.5, tau_l=0.8, tau_v=0.8, rho_l=1.0, rho_v=0.1, sigma=0.01,
+    base = dict(dt=DT_GRID, tau_l=0.8, tau_v=0.8, rho_l=1.0, rho_v=0.1, sigma=0.01,
                 xi=4.0, mobility=0.02, theta_deg=(90.0, 90.0))
     base.update(kw)
     base["theta_deg"] = tuple(float(t) for t in base["theta_deg"])
@@ -195,7 +204,7 @@ def _sessile(name, nx, ny, seed, R, jitter=0.2, theta=90.0, ratio=10.0, steps=20
 
 def sessile_droplet_64x32(seed=0):
     """Semicircular droplet R=12 on the bottom wall of a 64x32 box, 90 degree
-    walls, density ratio 10, tau 0.8, sigma 0.01, M 0.02, dt 0.5, 2000 steps."""
+    walls, density ratio 10, tau 0.8, sigma 0.01, M 0.02, dt 0.25, 2000 steps."""
     return _sessile("sessile droplet 64x32", 64, 32, seed, 12.0)
 
 
@@ -213,10 +222,10 @@ def small_sessile(nx=32, ny=16, seed=11, R=7.0, theta=90.0, jitter=0.2, steps=50
 def free_droplet_256(seed=1, n=256, R=48.0, steps=20000):
     """Static free droplet in a doubly periodic n x n box meshed with 4
     triangles per cell (131,585 grid points at n=256), jitter 0.25h, R=48,
-    xi 4, density ratio 100, tau 0.6, sigma 0.005, M 0.02, dt 0.5."""
+    xi 4, density ratio 100, tau 0.6, sigma 0.005, M 0.02, dt 0.1."""
     mesh = cross_mesh(n, n, 0.25, seed)
     centre = (n / 2.0, n / 2.0)
-    phys = _phys(rho_v=0.01, tau_l=0.6, tau_v=0.6, sigma=0.005, theta_deg=())
+    phys = _phys(dt=DT_CROSS, rho_v=0.01, tau_l=0.6, tau_v=0.6, sigma=0.005, theta_deg=())
     C0 = droplet_C0(mesh["xy"], centre, R, phys["xi"], mesh["period"])
     return {"name": f"free droplet {n}x{n}", "mesh": mesh, "C0": C0, "phys": phys,
             "steps": steps, "centre": centre, "R": float(R)}
@@ -226,7 +235,7 @@ def small_free_droplet(n=24, R=6.0, seed=5, steps=50, ratio=10.0, sigma=0.01):
     """A small doubly periodic free droplet for quick checks."""
     mesh = cross_mesh(n, n, 0.25, seed)
     centre = (n / 2.0, n / 2.0)
-    phys = _phys(rho_v=1.0 / ratio, sigma=sigma, theta_deg=())
+    phys = _phys(dt=DT_CROSS, rho_v=1.0 / ratio, sigma=sigma, theta_deg=())
     C0 = droplet_C0(mesh["xy"], centre, R, phys["xi"], mesh["period"])
     return {"name": f"free droplet {n}x{n}", "mesh": mesh, "C0": C0, "phys": phys,
             "steps": steps, "centre": centre, "R": float(R)}

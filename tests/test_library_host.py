@@ -1,0 +1,89 @@
+"""Host-side checks of the C-ABI library (no GPU needed): the shared library
+loads, exports every function ``include/felbm.h`` declares, validates meshes,
+derives the model constants, and builds the node tables."""
+import ctypes
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_1708_04678_gb300 import build as B
+from paper_1708_04678_gb300 import felbm as F
+from paper_1708_04678_gb300 import inputs as I
+
+HEADER = os.path.join(B.INCLUDE, "felbm.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return F.lib()
+
+
+def _declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(felbm_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_header_symbols_are_exported(lib):
+    names = _declared_functions()
+    assert "felbm_step" in names and "felbm_mesh_create" in names
+    for name in names:
+        assert hasattr(lib, name), name
+
+
+def test_params_derive_closed_forms(lib):
+    # xi = sqrt(8 kappa / beta), sigma = sqrt(2 kappa beta) / 6, cos(theta) = -phi_c / sqrt(2 kappa beta)
+    phys = dict(dt=0.5, tau_l=0.8, tau_v=0.8, rho_l=1.0, rho_v=0.1, sigma=0.01, xi=4.0,
+                mobility=0.02, theta_deg=(60.0, 90.0, 120.0))
+    p = F.params_derive(phys)
+    assert math.isclose(math.sqrt(8 * p.kappa / p.beta), 4.0, rel_tol=1e-14)
+    assert math.isclose(math.sqrt(2 * p.kappa * p.beta) / 6, 0.01, rel_tol=1e-14)
+    for k, th in enumerate((60.0, 90.0, 120.0)):
+        assert math.isclose(-p.phi_c[k] / math.sqrt(2 * p.kappa * p.beta), math.cos(math.radians(th)),
+                            rel_tol=1e-12, abs_tol=1e-15)
+    assert p.n_wall_ids == 3
+
+
+def test_mesh_tables(lib):
+    w = I.sessile_droplet_64x32()
+    mesh = F.Mesh.from_dict(w["mesh"])
+    info = mesh.info()
+    assert info["n_nodes"] == 64 * 33 and info["n_tri"] == 2 * 64 * 32
+    assert info["n_wall_edges"] == 128
+    assert info["max_degree"] == 7                       # 6 neighbours + itself on the '/' grid
+    assert info["nnz"] == 7 * 64 * 33 - 2 * 64 * 2      # wall rows have 5 entries
+    assert abs(info["total_area"] - 64 * 32) < 1e-9
+    assert info["bandwidth"] < 3 * 64                   # reverse Cuthill-McKee keeps rows near the diagonal
+    p = F.params_derive(w["phys"])
+    assert mesh.workspace_bytes(p) > 18 * 8 * info["n_nodes"]
+
+
+def test_mesh_validation(lib):
+    xy = np.array([[0.0, 0.0], [1.0, 0.0], [1.0, 1.0], [0.0, 1.0]])
+    walls = np.array([[0, 1], [1, 2], [2, 3], [3, 0]])
+    F.Mesh(xy, [[0, 1, 2], [0, 2, 3]], walls, [0, 0, 0, 0])           # valid square
+    with pytest.raises(F.FelbmError) as e:                            # clockwise triangle
+        F.Mesh(xy, [[0, 2, 1], [0, 2, 3]], walls, [0, 0, 0, 0])
+    assert e.value.code == -2
+    with pytest.raises(F.FelbmError) as e:                            # open edge not declared a wall
+        F.Mesh(xy, [[0, 1, 2], [0, 2, 3]], walls[:3], [0, 0, 0])
+    assert e.value.code == -2
+    with pytest.raises(F.FelbmError) as e:                            # node id out of range
+        F.Mesh(xy, [[0, 1, 7], [0, 2, 3]], walls, [0, 0, 0, 0])
+    assert e.value.code == -1
+    with pytest.raises(F.FelbmError) as e:                            # wall edge inside the mesh
+        F.Mesh(xy, [[0, 1, 2], [0, 2, 3]], np.vstack([walls, [[0, 2]]]), [0, 0, 0, 0, 0])
+    assert e.value.code == -2
+
+
+def test_periodic_mesh_min_image(lib):
+    m = I.cross_mesh(16, 16, 0.25, 1)
+    mesh = F.Mesh.from_dict(m)
+    info = mesh.info()
+    assert info["n_nodes"] == 512 and info["n_wall_edges"] == 0
+    assert abs(info["total_area"] - 256.0) < 1e-9
+    assert abs(info["min_area"] - m["min_area"]) < 1e-12
