@@ -148,8 +148,71 @@ def peaks():
 
 
 # --------------------------------------------------------------- GPU arm --
+def time_precision(F, torch, w, dev, precision, K, W, flush, barrier, world, dist):
+    """Build a state of the workload in one precision, run W warm-up steps and
+    K timed steps (L2 flushed before each), then K end-to-end steps through
+    host buffers.  Returns the measurements of this rank."""
+    mesh = F.Mesh.from_dict(w["mesh"])
+    prm = F.params_derive(w["phys"], precision=precision)
+    stream = torch.cuda.Stream(dev)
+    st = F.State(mesh, prm, w["C0"], device=dev, stream=stream)
+    st.timing_enable(True)
+    for k in range(W):
+        with torch.cuda.stream(stream):
+            flush.fill_(k & 255)
+        st.step(1)
+    stream.synchronize()
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    phases = []
+    torch.cuda.synchronize()
+    barrier()
+    for k in range(K):
+        with torch.cuda.stream(stream):
+            flush.fill_(k & 255)
+        ev0[k].record(stream)
+        st.step(1)
+        ev1[k].record(stream)
+        phases.append(st.timing_get())           # synchronises the stream
+    torch.cuda.synchronize()
+    barrier()
+    total_ms = sum(ev0[k].elapsed_time(ev1[k]) for k in range(K))
+    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    total_ms = float(t.item())
+    diag = st.diagnostics(w["centre"], w["R"], w["phys"]["xi"])
+
+    # end to end through the public API with host buffers: pinned g, h in,
+    # one step, the diagnostics (the step's metrics) out
+    g0, h0 = st.get_state()
+    gp = torch.from_numpy(g0).pin_memory()
+    hp = torch.from_numpy(h0).pin_memory()
+    for _ in range(2):
+        st.set_state(gp, hp)
+        st.step(1)
+        st.diagnostics()
+    torch.cuda.synchronize()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(K):
+        st.set_state(gp, hp)
+        st.step(1)
+        st.diagnostics()
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    e = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(e, op=dist.ReduceOp.MAX)
+    e2e_s = float(e.item())
+    ph = {k: statistics.mean(p[k] for p in phases) for k in phases[0] if k.endswith("_ms")}
+    info = mesh.info()
+    st.close()
+    return {"total_ms": total_ms, "e2e_s": e2e_s, "phase_ms": ph, "launches": phases[0]["launches"],
+            "solve_launches": phases[0]["solve_launches"], "info": info, "diag": diag}
+
+
 def run_gpu(args):
-    import numpy as np
     import torch
     import torch.distributed as dist
 
@@ -173,120 +236,76 @@ def run_gpu(args):
     if rank == 0 and not args.no_cpu_baseline:
         cpu = cpu_baseline_subprocess(args.cpu_seconds)
 
-    w = workload()
-    N = len(w["mesh"]["xy"])
-    mesh = F.Mesh.from_dict(w["mesh"])
-    prm = F.params_derive(w["phys"])
-    stream = torch.cuda.Stream(dev)
-    st = F.State(mesh, prm, w["C0"], device=dev, stream=stream)
-    st.timing_enable(True)
-    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
-
     def barrier():
         if world > 1:
             dist.barrier()
 
-    for k in range(max(args.warmup, 3)):
-        with torch.cuda.stream(stream):
-            flush.fill_(k & 255)
-        st.step(1)
-    stream.synchronize()
-
-    K = args.steps
-    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
-    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
-    phases = []
-    torch.cuda.synchronize()
-    barrier()
+    w = workload()
+    N = len(w["mesh"]["xy"])
+    K, W = args.steps, max(args.warmup, 3)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     with ClockSampler(local) as clk:
-        for k in range(K):
-            with torch.cuda.stream(stream):
-                flush.fill_(k & 255)
-            ev0[k].record(stream)
-            st.step(1)
-            ev1[k].record(stream)
-            phases.append(st.timing_get())           # synchronises the stream
-        torch.cuda.synchronize()
-        barrier()
-    step_ms = [ev0[k].elapsed_time(ev1[k]) for k in range(K)]
-    total_ms = sum(step_ms)
-    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    total_ms = float(t.item())
+        r32 = time_precision(F, torch, w, dev, F.FP32_DEV, K, W, flush, barrier, world, dist)
+        r64 = time_precision(F, torch, w, dev, F.FP64, K, W, flush, barrier, world, dist)
 
-    # end to end through the public API with host buffers: pinned g, h in,
-    # one step, diagnostics (the step's metrics) out
-    g0, h0 = st.get_state()
-    gp = torch.from_numpy(g0).pin_memory()
-    hp = torch.from_numpy(h0).pin_memory()
-    for _ in range(2):
-        st.set_state(gp, hp)
-        st.step(1)
-        st.diagnostics()
-    torch.cuda.synchronize()
-    barrier()
-    t0 = time.perf_counter()
-    for _ in range(K):
-        st.set_state(gp, hp)
-        st.step(1)
-        st.diagnostics()
-    torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
-    e = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(e, op=dist.ReduceOp.MAX)
-    e2e_s = float(e.item())
-
+    for name, r in (("FP32", r32), ("FP64", r64)):
+        if r["diag"]["status"] != 0:
+            raise SystemExit(f"bench: the {name} state is not finite after the timed steps")
     if rank == 0:
-        ph = {k: statistics.mean(p[k] for p in phases) for k in phases[0] if k.endswith("_ms")}
-        launches = phases[0]["launches"]
-        solve_launches = phases[0]["solve_launches"]
-        info = mesh.info()
-        nnz = info["nnz"]
-        # dominant kernel: one Chebyshev sweep of the mass solve
-        sweep_ms = ph["solve_ms"] / solve_launches
-        # algorithmic bytes of one sweep: gathered x_k, own x_{k-1}, rhs, new x
-        # (4 x 18 doubles per node) + the mass row (column index, value) +
-        # row pointer and inverse lumped mass
-        alg_bytes = N * 4 * 18 * 8 + nnz * (4 + 8) + N * (4 + 8)
-        alg_flops = nnz * 18 * 2 + N * 18 * 6
+        nnz = r32["info"]["nnz"]
+        # dominant kernel of the FP32-deviation step: one FP32 Chebyshev sweep
+        # of the 18-RHS mass solve (the last sweep also updates the fields)
+        sweep_ms = r32["phase_ms"]["solve_ms"] / r32["solve_launches"]
+        # algorithmic bytes of one sweep: gathered x_k, own x_{k-1}, rhs, new
+        # x (4 x 18 floats per node), the mass row (column index + FP32 value
+        # per entry), row pointer and inverse lumped mass per node
+        alg_bytes = N * 4 * 18 * 4 + nnz * (4 + 4) + N * (4 + 4)
         hbm_peak, peak_src = peaks()
-        achieved_gbs = alg_bytes / (sweep_ms * 1e-3) / 1e9
-        value = N * K * world / (total_ms * 1e-3)
-        e2e_value = N * K * world / e2e_s
+        achieved = alg_bytes / (sweep_ms * 1e-3) / 1e9
+
+        def summary(r, dtype):
+            return {"value": N * K * world / (r["total_ms"] * 1e-3), "ms_per_step": r["total_ms"] / K,
+                    "dtype": dtype, "phase_ms": {k: round(v, 5) for k, v in r["phase_ms"].items()},
+                    "launches_per_step": r["launches"],
+                    "e2e_value": N * K * world / r["e2e_s"],
+                    "after_timed_steps": {k: r["diag"][k] for k in ("max_u", "delta_p", "mass_drift_rel",
+                                                                    "interface_rho_uu", "status")}}
+
+        s32, s64 = summary(r32, "f32 (FP64 C, mu, reductions)"), summary(r64, "f64")
         out = {
             "metric": METRIC,
-            "value": value,
+            "value": s32["value"],
             "unit": "node-updates/s",
             "n_gpus": world,
             "steps": K,
-            "warmup": max(args.warmup, 3),
-            "ms_per_step": total_ms / K,
+            "warmup": W,
+            "ms_per_step": s32["ms_per_step"],
             "higher_is_better": True,
             "scaling": "weak",
             "vs_baseline": None,
-            "dtype": "f64",
+            "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": w["name"] + " free droplet, 131,585 grid points, 4 tri/cell, jitter 0.25h, FP64",
-                       "nodes": N, "triangles": info["n_tri"], "dt": w["phys"]["dt"],
-                       "solver_sweeps": solve_launches + 1, "l2": "flushed before every timed step (256 MiB write)",
+            "config": {"workload": "free droplet 256x256: 131,585 grid points (131,072 nodes), 4 tri/cell, "
+                                   "jitter 0.25h, rho ratio 100, FP32 deviation storage",
+                       "nodes": N, "triangles": r32["info"]["n_tri"], "dt": w["phys"]["dt"],
+                       "solver": f"FP32 Chebyshev, {r32['solve_launches'] + 1} sweeps",
+                       "l2": "flushed before every timed step (256 MiB write)",
                        "parallelism": f"replicas x{world}"},
-            "phase_ms": {k: round(v, 5) for k, v in ph.items()},
-            "roofline": {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm_peak,
-                         "unit": "GB/s", "frac": achieved_gbs / hbm_peak, "traffic": None,
-                         "kernel": "k_cheb (one Chebyshev sweep of the 18-RHS mass solve)",
-                         "alg_bytes_per_launch": alg_bytes, "alg_flops_per_launch": alg_flops,
-                         "launch_ms": sweep_ms, "peak_source": peak_src},
-            "e2e": {"value": e2e_value, "unit": "node-updates/s",
+            "fp32_dev": s32,
+            "fp64": s64,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                         "frac": achieved / hbm_peak, "traffic": None,
+                         "kernel": "k_cheb32 (one FP32 Chebyshev sweep of the 18-RHS mass solve)",
+                         "alg_bytes_per_launch": alg_bytes, "launch_ms": sweep_ms,
+                         "peak_source": peak_src},
+            "e2e": {"value": s32["e2e_value"], "unit": "node-updates/s",
                     "h2d_bytes_per_step": 2 * 9 * N * 8, "d2h_bytes_per_step": 112},
-            "gpu_launches": launches * K,
+            "gpu_launches": r32["launches"] * K,
             "clocks": clk.summary(),
         }
         if cpu is not None:
             out["cpu_baseline"] = cpu
         print(json.dumps(out), flush=True)
-    st.close()
     if world > 1:
         dist.destroy_process_group()
 

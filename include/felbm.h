@@ -50,8 +50,21 @@ extern "C" {
 #define FELBM_LAP_CONSISTENT 0
 #define FELBM_LAP_PAPER 1
 
-/* Storage/arithmetic of the distributions. */
+/* Storage/arithmetic of the distributions.
+ * FP64:     g, h stored and updated in FP64.
+ * FP32_DEV: the fields C (FP64), p, u (FP32) plus the FP32 deviations of g, h
+ *           from their equilibria; FP32 arithmetic except the chemical
+ *           potential (double well and Laplacian of C) and the C update, which
+ *           stay FP64; the mass solve runs in FP32 (solver_rounds must be 0/1). */
 #define FELBM_FP64 0
+#define FELBM_FP32_DEV 1
+
+/* Consistent-mass solve (Sec. II.C: M11 with the lumped-mass preconditioner).
+ * MIXED: iterative refinement -- FP32 Chebyshev corrections, residual carried
+ *        in FP64 (default; reaches FP64 round-off with solver_rounds = 3).
+ * FP64:  Chebyshev sweeps in FP64 throughout. */
+#define FELBM_SOLVER_MIXED 0
+#define FELBM_SOLVER_FP64 1
 
 /* Model constants (Sec. II of the paper, lattice units).
  *  dt              time step (characteristic step eqn::integrated)
@@ -61,9 +74,13 @@ extern "C" {
  *  mobility        Cahn-Hilliard mobility M (eqn:mp_che)
  *  phi_c[id]       wetting potential of wall id (eqn:bc2); cos(theta) = -phi_c / sqrt(2 kappa beta)
  *  lap_mode        FELBM_LAP_CONSISTENT or FELBM_LAP_PAPER
- *  precision       FELBM_FP64
- *  solver_iters    Chebyshev sweeps of the mass-matrix solve (0 = 32: error
- *                  bound 2*3^-32 relative in the energy norm)            */
+ *  precision       FELBM_FP64 or FELBM_FP32_DEV
+ *  solver_mode     FELBM_SOLVER_MIXED or FELBM_SOLVER_FP64
+ *  solver_iters    Chebyshev sweeps per correction (MIXED, 0 = 14, error
+ *                  bound 2*3^-14 per correction) or in total (FP64, 0 = 32,
+ *                  bound 2*3^-32); >= 2
+ *  solver_rounds   corrections of the MIXED solve (0 = 3 for FP64 storage,
+ *                  1 for FP32_DEV)                                         */
 typedef struct felbm_params {
     double dt;
     double tau_l, tau_v;
@@ -74,7 +91,9 @@ typedef struct felbm_params {
     int32_t n_wall_ids;
     int32_t lap_mode;
     int32_t precision;
+    int32_t solver_mode;
     int32_t solver_iters;
+    int32_t solver_rounds;
 } felbm_params;
 
 typedef struct felbm_mesh felbm_mesh;
@@ -175,8 +194,8 @@ int felbm_set_state(felbm_state* state, const double* g, const double* h);
 int felbm_get_fields(felbm_state* state, double* C, double* p, double* ux, double* uy, double* mu);
 
 /* Solve M11 X = B for k right-hand sides with the state's mass matrix and
- * the same Chebyshev iteration felbm_step uses (Sec. II.C: consistent mass
- * matrix, lumped-mass preconditioner).  B, X: double [k][n_nodes] host,
+ * the same solver felbm_step uses (Sec. II.C: consistent mass matrix,
+ * lumped-mass preconditioner).  B, X: double [k][n_nodes] host,
  * caller order; 1 <= k <= 18.  Uses the state's scratch buffers; do not
  * overlap with felbm_step on another stream.  Synchronises. */
 int felbm_mass_solve(felbm_state* state, const double* B, double* X, int32_t k);

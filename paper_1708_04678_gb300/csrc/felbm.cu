@@ -57,10 +57,11 @@ __host__ __device__ constexpr int opp(int q) {
 static_assert(opp(1) == 3 && opp(2) == 4 && opp(3) == 1 && opp(4) == 2, "opp");
 static_assert(opp(5) == 7 && opp(6) == 8 && opp(7) == 5 && opp(8) == 6, "opp");
 
-// e.v for a compile-time direction: only additions
-template <int q>
-__device__ __forceinline__ double edot(double vx, double vy) {
-    double r = 0.0;
+// e.v for a compile-time direction: only additions, in the type of v (an
+// FP32 caller must not be promoted to FP64 -- GB300 runs FP64 at 1/64 rate)
+template <int q, class T>
+__device__ __forceinline__ T edot(T vx, T vy) {
+    T r = T(0);
     if (ex(q) == 1) r = vx;
     if (ex(q) == -1) r = -vx;
     if (ey(q) == 1) r = r + vy;
@@ -75,18 +76,24 @@ struct DevMesh {
     const int32_t* tri;       // [3][Tp]
     const double* area;       // [Tp]
     const double* grad;       // [6][Tp]
+    const float* area32;      // [Tp]   FP32 copies for the FP32-deviation path
+    const float* grad32;      // [6][Tp]
     const int32_t* nbr;       // [3][Tp]
     const int32_t* row_ptr;   // [N+1]
     const int32_t* col;       // [nnz]
     const double* mval;       // [nnz] consistent mass
     const double* lval;       // [nnz] -2 K_ij / V_i (patch Laplacian of C)
     const double* inv_lumped; // [Np]
+    const float* mval32;      // [nnz] FP32 copy of the mass entries
+    const float* inv_lumped32;// [Np]
     const double* lumped;     // [Np]
     const double* inv_vol;    // [Np] 1 / V_i
     const int32_t* inc_ptr;   // [N+1]
     const int32_t* inc_tri;   // [ninc]
     const double* inc_bx;     // [ninc]
     const double* inc_by;     // [ninc]
+    const float* inc_bx32;    // [ninc]
+    const float* inc_by32;    // [ninc]
     const int32_t* wall_a;    // [E]
     const int32_t* wall_b;
     const int32_t* wall_id;
@@ -104,6 +111,8 @@ struct DevMesh {
 struct Phys {
     double dt, tau_l, tau_v, rho_l, rho_v, kappa, beta, mobility;
     double phi_c[FELBM_MAX_WALL_IDS];
+    // FP32 copies, rounded once on the host
+    float dt_f, dt3_f, dt2h_f, inv_tau_l_f, inv_tau_v_f, rho_v_f, drho_f, mobility_f;
 };
 
 struct Bufs {
@@ -116,8 +125,21 @@ struct Bufs {
     double* gmu;     // [2][Tp]
     double* R;       // [T][18]
     double* rhs;     // [18][Np]
-    double* x0;      // [18][Np]
-    double* x1;      // [18][Np]
+    double* x0;      // [18][Np] FP64 Chebyshev iterates; in the mixed solve
+    double* x1;      // [18][Np] they hold x64 (solution) and rho64 (residual)
+    double* x64;     // alias of x0
+    double* rho64;   // alias of x1
+    float* r32;      // [18][Np] FP32 residual of the current correction
+    float* e0;       // [18][Np] FP32 Chebyshev iterates
+    float* e1;
+    // FP32-deviation storage (precision FELBM_FP32_DEV); C above stays FP64
+    float* dpsi;     // [18][Np] deviations from equilibrium
+    float* p32;      // [Np]
+    float* ux32;
+    float* uy32;
+    float* mu32;
+    float* gmu32;    // [2][Tp]
+    float* R32;      // [T][18]
     double* stage;   // [18][Np] caller-order staging
     double* diag_part; // [kDiagBlocks][kDiagSlots]
     double* diag_out;  // [kDiagSlots]
@@ -293,7 +315,10 @@ __global__ void __launch_bounds__(128) k_element(DevMesh m, Phys c, Bufs b) {
 // RHS_{i,a} = sum_{T at i} R_{T,a} (dt/3 + dt^2/2 e_a.b_{i,T})
 //           - dt sum_{wall e at i} (e_a.n) [L/3 (psi_opp - psi)_i + L/6 (psi_opp - psi)_o]
 // (second sum only for incoming directions e_a.n < 0; o = other end of e).
-// Also writes the first Chebyshev iterate x1 = RHS / (m_i theta).
+// Also writes the first Chebyshev iterate x1 = RHS / (m_i theta): in FP64
+// (FP64 Chebyshev) or, for the mixed-precision solve, in FP32 together with
+// the FP32 copy of the right-hand side.
+template <bool kMixed>
 __global__ void __launch_bounds__(128) k_rhs(DevMesh m, Phys c, Bufs b, double inv_theta) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= m.N) return;
@@ -348,18 +373,32 @@ __global__ void __launch_bounds__(128) k_rhs(DevMesh m, Phys c, Bufs b, double i
 #pragma unroll
     for (int q = 0; q < 18; ++q) {
         b.rhs[q * Np + i] = acc[q];
-        b.x1[q * Np + i] = acc[q] * s;
+        if (kMixed) {
+            b.r32[q * Np + i] = (float)acc[q];
+            b.e1[q * Np + i] = (float)(acc[q] * s);
+        } else {
+            b.x1[q * Np + i] = acc[q] * s;
+        }
     }
 }
 
 // First Chebyshev iterate for a standalone solve: x1 = B / (m_i theta).
+template <bool kMixed>
 __global__ void __launch_bounds__(kBlock) k_cheb_start(DevMesh m, Bufs b, double inv_theta) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= m.N) return;
     const int Np = m.Np;
     double s = m.inv_lumped[i] * inv_theta;
 #pragma unroll
-    for (int q = 0; q < 18; ++q) b.x1[q * Np + i] = b.rhs[q * Np + i] * s;
+    for (int q = 0; q < 18; ++q) {
+        double r = b.rhs[q * Np + i];
+        if (kMixed) {
+            b.r32[q * Np + i] = (float)r;
+            b.e1[q * Np + i] = (float)(r * s);
+        } else {
+            b.x1[q * Np + i] = r * s;
+        }
+    }
 }
 
 // ---------------------------------------------- K6: Chebyshev sweep -------
@@ -393,6 +432,82 @@ __global__ void __launch_bounds__(128) k_cheb(DevMesh m, Bufs b, const double* _
             b.psi[q * Np + i] += xn;
         else
             prev[q * Np + i] = xn;
+    }
+}
+
+// ------------------------------- K6': mixed-precision mass solve ---------
+// Iterative refinement: x <- x + e, where each correction e solves
+// M11 e = rho approximately with FP32 Chebyshev sweeps (same recurrence as
+// k_cheb, FP32 matrix copy), and the residual rho is carried in FP64 by the
+// recurrence rho <- rho - M11 e with M11 in FP64.  GB300 runs FP32 FMA at
+// ~70x the FP64 rate, so only the refinement kernels pay FP64 matvecs.
+enum Final { kStore = 0, kAddPsi = 1, kAddX64 = 2, kUpdateDev = 3 };
+
+#include "felbm_dev32.cuh"
+
+template <int kFinal>
+__global__ void __launch_bounds__(128) k_cheb32(DevMesh m, Phys c, Bufs b, const float* __restrict__ cur,
+                                                float* prev, float a, float cc, int first, int have_x64) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m.N) return;
+    const int Np = m.Np;
+    float acc[18];
+#pragma unroll
+    for (int q = 0; q < 18; ++q) acc[q] = 0.0f;
+    for (int k = m.row_ptr[i]; k < m.row_ptr[i + 1]; ++k) {
+        int j = m.col[k];
+        float mv = m.mval32[k];
+#pragma unroll
+        for (int q = 0; q < 18; ++q) acc[q] = fmaf(mv, cur[q * Np + j], acc[q]);
+    }
+    float s = cc * m.inv_lumped32[i];
+    float d[18];
+#pragma unroll
+    for (int q = 0; q < 18; ++q) {
+        float xk = cur[q * Np + i];
+        float xm = first ? 0.0f : prev[q * Np + i];
+        float xn = xk + a * (xk - xm) + s * (b.r32[q * Np + i] - acc[q]);
+        if (kFinal == kStore) {
+            prev[q * Np + i] = xn;
+        } else if (kFinal == kUpdateDev) {
+            d[q] = xn;
+        } else {
+            double x = have_x64 ? b.x64[q * Np + i] + (double)xn : (double)xn;
+            if (kFinal == kAddPsi)
+                b.psi[q * Np + i] += x;
+            else
+                b.x64[q * Np + i] = x;
+        }
+    }
+    if (kFinal == kUpdateDev) dev32_update(m, c, b, i, d);
+}
+
+// x <- x + e ; rho <- rho - M11 e (FP64) ; FP32 copy of rho and the first
+// Chebyshev iterate of the next correction, rho / (m theta).
+__global__ void __launch_bounds__(128) k_refine(DevMesh m, Bufs b, const float* __restrict__ e,
+                                                float* next_first, int first_round, double inv_theta) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m.N) return;
+    const int Np = m.Np;
+    double acc[18];
+#pragma unroll
+    for (int q = 0; q < 18; ++q) acc[q] = 0.0;
+    for (int k = m.row_ptr[i]; k < m.row_ptr[i + 1]; ++k) {
+        int j = m.col[k];
+        double mv = m.mval[k];
+#pragma unroll
+        for (int q = 0; q < 18; ++q) acc[q] += mv * (double)e[q * Np + j];
+    }
+    double s = m.inv_lumped[i] * inv_theta;
+#pragma unroll
+    for (int q = 0; q < 18; ++q) {
+        double xo = first_round ? 0.0 : b.x64[q * Np + i];
+        double ro = first_round ? b.rhs[q * Np + i] : b.rho64[q * Np + i];
+        double rn = ro - acc[q];
+        b.x64[q * Np + i] = xo + (double)e[q * Np + i];
+        b.rho64[q * Np + i] = rn;
+        b.r32[q * Np + i] = (float)rn;
+        next_first[q * Np + i] = (float)(rn * s);
     }
 }
 
@@ -476,22 +591,36 @@ __device__ void block_reduce_store(double (&s)[NS], double (&mx)[NM], double* ou
     }
 }
 
+template <bool kDev32>
 __global__ void __launch_bounds__(kBlock) k_diag_nodes(DevMesh m, Phys c, Bufs b, DiagReq rq) {
     double s[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
     double mx[1] = {0.0};
     const int Np = m.Np;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m.N; i += gridDim.x * blockDim.x) {
-        double C = 0, p = 0, g[9];
+        double C = 0, p = 0, ux, uy, rho;
+        if (kDev32) {
+            C = b.C[i];
+            p = b.p32[i];
+            ux = b.ux32[i];
+            uy = b.uy32[i];
+            rho = c.rho_v + C * (c.rho_l - c.rho_v);
+            float dsum = 0.0f;
+            for (int q = 0; q < 18; ++q) dsum += b.dpsi[q * Np + i];
+            if (!isfinite(dsum)) p = dsum;   // non-finite deviations are reported too
+        } else {
+            double g[9];
 #pragma unroll
-        for (int q = 0; q < 9; ++q) {
-            g[q] = b.psi[q * Np + i];
-            p += g[q];
-            C += b.psi[(9 + q) * Np + i];
+            for (int q = 0; q < 9; ++q) {
+                g[q] = b.psi[q * Np + i];
+                p += g[q];
+                C += b.psi[(9 + q) * Np + i];
+            }
+            double mxm = (g[1] - g[3]) + (g[5] - g[6]) + (g[8] - g[7]);
+            double mym = (g[2] - g[4]) + (g[5] + g[6]) - (g[7] + g[8]);
+            rho = c.rho_v + C * (c.rho_l - c.rho_v);
+            ux = 3.0 * mxm / rho;
+            uy = 3.0 * mym / rho;
         }
-        double mxm = (g[1] - g[3]) + (g[5] - g[6]) + (g[8] - g[7]);
-        double mym = (g[2] - g[4]) + (g[5] + g[6]) - (g[7] + g[8]);
-        double rho = c.rho_v + C * (c.rho_l - c.rho_v);
-        double ux = 3.0 * mxm / rho, uy = 3.0 * mym / rho;
         double uu = ux * ux + uy * uy;
         double w = m.lumped[i];
         b.Cdiag[i] = C;
@@ -550,17 +679,19 @@ __global__ void __launch_bounds__(kBlock) k_diag_edges(DevMesh m, Bufs b, DiagRe
     block_reduce_store<1, 1>(s, mx, b.diag_part + (size_t)blockIdx.x * kDiagSlots + 11);
 }
 
+// One warp per slot: lane l reduces blocks l, l+32, ... in order, then a
+// fixed shuffle tree -- the same order on every call.
 __global__ void k_diag_final(Bufs b) {
-    // one thread per slot, blocks summed in index order
-    int k = threadIdx.x;
+    int k = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (k >= 13) return;
     bool is_max = (k == 10 || k == 12);
-    double r = b.diag_part[k];
-    for (int blk = 1; blk < kDiagBlocks; ++blk) {
+    double r = is_max ? -1e300 : 0.0;
+    for (int blk = lane; blk < kDiagBlocks; blk += 32) {
         double v = b.diag_part[(size_t)blk * kDiagSlots + k];
         r = is_max ? fmax(r, v) : r + v;
     }
-    b.diag_out[k] = r;
+    r = is_max ? warp_max(r) : warp_sum(r);
+    if (lane == 0) b.diag_out[k] = r;
 }
 
 // --------------------------------------------------------- host side ------
@@ -604,7 +735,9 @@ struct felbm_state {
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t graph_exec = nullptr;
     cudaGraph_t graph = nullptr;
-    int sweeps = 32;
+    int mode = FELBM_SOLVER_MIXED;
+    int sweeps = 14;   // per correction (mixed) or in total (FP64)
+    int rounds = 3;    // corrections of the mixed solve
     std::vector<double> cheb_a, cheb_c;
     double inv_theta = 1.0;
     int64_t step = 0;
@@ -613,12 +746,13 @@ struct felbm_state {
     bool timing = false;
     bool timed_step_ran = false;
     cudaEvent_t ev[7] = {};
+    bool dev32 = false;   // FELBM_FP32_DEV storage
 };
 
 namespace felbm {
 
 // Layout of the workspace; with base == nullptr only the size is computed.
-static size_t carve(const HostMesh& h, void* base, DevMesh* dm, Bufs* b) {
+static size_t carve(const HostMesh& h, bool dev32, void* base, DevMesh* dm, Bufs* b) {
     Carver cv(base);
     size_t Np = pad64(h.N), Tp = pad64(h.T);
     size_t nnz = h.row_ptr[h.N], ninc = h.inc_ptr[h.N], nwinc = h.winc_ptr[h.N];
@@ -627,18 +761,24 @@ static size_t carve(const HostMesh& h, void* base, DevMesh* dm, Bufs* b) {
     d.tri = cv.take<int32_t>(3 * Tp);
     d.area = cv.take<double>(Tp);
     d.grad = cv.take<double>(6 * Tp);
+    d.area32 = cv.take<float>(Tp);
+    d.grad32 = cv.take<float>(6 * Tp);
     d.nbr = cv.take<int32_t>(3 * Tp);
     d.row_ptr = cv.take<int32_t>(h.N + 1);
     d.col = cv.take<int32_t>(nnz);
     d.mval = cv.take<double>(nnz);
     d.lval = cv.take<double>(nnz);
     d.inv_lumped = cv.take<double>(Np);
+    d.mval32 = cv.take<float>(nnz);
+    d.inv_lumped32 = cv.take<float>(Np);
     d.lumped = cv.take<double>(Np);
     d.inv_vol = cv.take<double>(Np);
     d.inc_ptr = cv.take<int32_t>(h.N + 1);
     d.inc_tri = cv.take<int32_t>(ninc);
     d.inc_bx = cv.take<double>(ninc);
     d.inc_by = cv.take<double>(ninc);
+    d.inc_bx32 = cv.take<float>(ninc);
+    d.inc_by32 = cv.take<float>(ninc);
     d.wall_a = cv.take<int32_t>(E);
     d.wall_b = cv.take<int32_t>(E);
     d.wall_id = cv.take<int32_t>(E);
@@ -652,17 +792,32 @@ static size_t carve(const HostMesh& h, void* base, DevMesh* dm, Bufs* b) {
     d.perm = cv.take<int32_t>(h.N);
     d.iperm = cv.take<int32_t>(h.N);
     Bufs bb{};
-    bb.psi = cv.take<double>(18 * Np);
     bb.C = cv.take<double>(Np);
-    bb.p = cv.take<double>(Np);
-    bb.ux = cv.take<double>(Np);
-    bb.uy = cv.take<double>(Np);
-    bb.mu = cv.take<double>(Np);
-    bb.gmu = cv.take<double>(2 * Tp);
-    bb.R = cv.take<double>(18 * (size_t)h.T);
+    if (!dev32) {
+        bb.psi = cv.take<double>(18 * Np);
+        bb.p = cv.take<double>(Np);
+        bb.ux = cv.take<double>(Np);
+        bb.uy = cv.take<double>(Np);
+        bb.mu = cv.take<double>(Np);
+        bb.gmu = cv.take<double>(2 * Tp);
+        bb.R = cv.take<double>(18 * (size_t)h.T);
+    } else {
+        bb.dpsi = cv.take<float>(18 * Np);
+        bb.p32 = cv.take<float>(Np);
+        bb.ux32 = cv.take<float>(Np);
+        bb.uy32 = cv.take<float>(Np);
+        bb.mu32 = cv.take<float>(Np);
+        bb.gmu32 = cv.take<float>(2 * Tp);
+        bb.R32 = cv.take<float>(18 * (size_t)h.T);
+    }
     bb.rhs = cv.take<double>(18 * Np);
     bb.x0 = cv.take<double>(18 * Np);
     bb.x1 = cv.take<double>(18 * Np);
+    bb.x64 = bb.x0;
+    bb.rho64 = bb.x1;
+    bb.r32 = cv.take<float>(18 * Np);
+    bb.e0 = cv.take<float>(18 * Np);
+    bb.e1 = cv.take<float>(18 * Np);
     bb.stage = cv.take<double>(18 * Np);
     bb.diag_part = cv.take<double>((size_t)kDiagBlocks * kDiagSlots);
     bb.diag_out = cv.take<double>(kDiagSlots);
@@ -684,12 +839,19 @@ static int check_params(const felbm_params* p) {
     if (!p || !(p->dt > 0.0) || !(p->tau_l > 0.0) || !(p->tau_v > 0.0) || !(p->rho_l > 0.0) ||
         !(p->rho_v > 0.0) || !(p->kappa >= 0.0) || !(p->beta >= 0.0) || !(p->mobility >= 0.0) ||
         p->lap_mode < 0 || p->lap_mode > 1 || p->solver_iters < 0 || p->solver_iters == 1 ||
+        p->solver_iters > 1000 || p->solver_rounds < 0 || p->solver_rounds > 20 ||
+        p->solver_mode < 0 || p->solver_mode > 1 ||
         p->n_wall_ids < 0 || p->n_wall_ids > FELBM_MAX_WALL_IDS) {
-        set_error("felbm: invalid params (dt, tau, rho > 0; kappa, beta, mobility >= 0; lap_mode 0/1; solver_iters 0 or >= 2)");
+        set_error("felbm: invalid params (dt, tau, rho > 0; kappa, beta, mobility >= 0; lap_mode 0/1; "
+                  "solver_mode 0/1; solver_iters 0 or 2..1000; solver_rounds 0..20)");
         return FELBM_ERR_INVALID_ARG;
     }
-    if (p->precision != FELBM_FP64) {
-        set_error("felbm: precision not supported by this build");
+    if (p->precision != FELBM_FP64 && p->precision != FELBM_FP32_DEV) {
+        set_error("felbm: unknown precision");
+        return FELBM_ERR_UNSUPPORTED;
+    }
+    if (p->precision == FELBM_FP32_DEV && (p->solver_mode != FELBM_SOLVER_MIXED || p->solver_rounds > 1)) {
+        set_error("felbm: FELBM_FP32_DEV solves in FP32 (solver_mode MIXED, solver_rounds 0 or 1)");
         return FELBM_ERR_UNSUPPORTED;
     }
     return FELBM_OK;
@@ -703,6 +865,61 @@ static cudaError_t up(const T* dst, const std::vector<T>& src, cudaStream_t s) {
 
 static unsigned grid_for(int n, int block) { return (unsigned)((n + block - 1) / block); }
 
+// Enqueue the mass solve for the right-hand side in b.rhs (first iterate
+// already written).  into_psi: add the increment to psi (time step); else
+// leave the solution in x1/x0 (FP64 mode, returned) or x64 (mixed mode).
+// bufs: the buffers the solve reads and writes (the state's own, or another
+// set of scratch buffers with the same layout).
+static const double* enqueue_solve(felbm_state* st, const Bufs& b, cudaStream_t s, bool into_psi) {
+    const DevMesh& m = st->dm;
+    const unsigned grid = grid_for(m.N, 128);
+    if (st->mode == FELBM_SOLVER_FP64) {
+        const double* result = b.x1;
+        for (int k = 1; k < st->sweeps; ++k) {
+            const double* cur = (k & 1) ? b.x1 : b.x0;
+            double* prev = (k & 1) ? b.x0 : b.x1;
+            k_cheb<<<grid, 128, 0, s>>>(m, b, cur, prev, st->cheb_a[k], st->cheb_c[k], k == 1,
+                                        into_psi && k == st->sweeps - 1);
+            result = prev;
+        }
+        return result;
+    }
+    float* A = b.e1;
+    float* B = b.e0;
+    const int have_x64 = st->rounds > 1;
+    for (int r = 0; r < st->rounds; ++r) {
+        float* cur = A;
+        float* prv = B;
+        for (int k = 1; k < st->sweeps; ++k) {
+            const float a = (float)st->cheb_a[k], c = (float)st->cheb_c[k];
+            const bool last = r == st->rounds - 1 && k == st->sweeps - 1;
+            const Phys& ph = st->phys;
+            if (!last)
+                k_cheb32<kStore><<<grid, 128, 0, s>>>(m, ph, b, cur, prv, a, c, k == 1, have_x64);
+            else if (!into_psi)
+                k_cheb32<kAddX64><<<grid, 128, 0, s>>>(m, ph, b, cur, prv, a, c, k == 1, have_x64);
+            else if (st->dev32)
+                k_cheb32<kUpdateDev><<<grid, 128, 0, s>>>(m, ph, b, cur, prv, a, c, k == 1, have_x64);
+            else
+                k_cheb32<kAddPsi><<<grid, 128, 0, s>>>(m, ph, b, cur, prv, a, c, k == 1, have_x64);
+            std::swap(cur, prv);
+        }
+        if (r < st->rounds - 1) {
+            k_refine<<<grid, 128, 0, s>>>(m, b, cur, prv, r == 0, st->inv_theta);
+            A = prv;
+            B = cur;
+        }
+    }
+    return b.x64;
+}
+
+static int solve_launches(const felbm_state* st) {
+    return st->mode == FELBM_SOLVER_FP64 ? st->sweeps - 1
+                                         : st->rounds * (st->sweeps - 1) + (st->rounds - 1);
+}
+
+static int step_launches(const felbm_state* st) { return (st->dev32 ? 4 : 5) + solve_launches(st); }
+
 // Enqueue the kernels of one time step on stream s (optionally with the
 // phase events, recorded as external event nodes of the captured graph).
 static void enqueue_step(felbm_state* st, cudaStream_t s) {
@@ -712,6 +929,21 @@ static void enqueue_step(felbm_state* st, cudaStream_t s) {
         if (st->timing) cudaEventRecordWithFlags(st->ev[k], s, cudaEventRecordExternal);
     };
     mark(0);
+    if (st->dev32) {
+        // collision is folded into the element, RHS and update kernels
+        mark(1);
+        k_mu32<<<grid_for(m.N, kBlock), kBlock, 0, s>>>(m, st->phys, b);
+        mark(2);
+        k_gradmu32<<<grid_for(m.T, kBlock), kBlock, 0, s>>>(m, b);
+        mark(3);
+        k_element32<<<grid_for(m.T, 128), 128, 0, s>>>(m, st->phys, b);
+        mark(4);
+        k_rhs32<<<grid_for(m.N, 128), 128, 0, s>>>(m, st->phys, b, (float)st->inv_theta);
+        mark(5);
+        enqueue_solve(st, st->buf, s, true);
+        mark(6);
+        return;
+    }
     k_collide<<<grid_for(m.N, kBlock), kBlock, 0, s>>>(m, st->phys, b, 1);
     mark(1);
     k_mu<<<grid_for(m.N, kBlock), kBlock, 0, s>>>(m, st->phys, b);
@@ -720,14 +952,12 @@ static void enqueue_step(felbm_state* st, cudaStream_t s) {
     mark(3);
     k_element<<<grid_for(m.T, 128), 128, 0, s>>>(m, st->phys, b);
     mark(4);
-    k_rhs<<<grid_for(m.N, 128), 128, 0, s>>>(m, st->phys, b, st->inv_theta);
+    if (st->mode == FELBM_SOLVER_FP64)
+        k_rhs<false><<<grid_for(m.N, 128), 128, 0, s>>>(m, st->phys, b, st->inv_theta);
+    else
+        k_rhs<true><<<grid_for(m.N, 128), 128, 0, s>>>(m, st->phys, b, st->inv_theta);
     mark(5);
-    for (int k = 1; k < st->sweeps; ++k) {
-        const double* cur = (k & 1) ? b.x1 : b.x0;
-        double* prev = (k & 1) ? b.x0 : b.x1;
-        k_cheb<<<grid_for(m.N, 128), 128, 0, s>>>(m, b, cur, prev, st->cheb_a[k], st->cheb_c[k], k == 1,
-                                                   k == st->sweeps - 1);
-    }
+    enqueue_solve(st, st->buf, s, true);
     mark(6);
 }
 
@@ -744,7 +974,7 @@ int felbm_workspace_bytes(const felbm_mesh* mesh, const felbm_params* params, si
     }
     int rc = check_params(params);
     if (rc) return rc;
-    *bytes = carve(mesh->h, nullptr, nullptr, nullptr);
+    *bytes = carve(mesh->h, params->precision == FELBM_FP32_DEV, nullptr, nullptr, nullptr);
     return FELBM_OK;
 }
 
@@ -763,7 +993,8 @@ int felbm_init(const felbm_mesh* mesh, const felbm_params* params, const double*
             set_error("felbm_init: a wall id has no phi_c (n_wall_ids too small)");
             return FELBM_ERR_INVALID_ARG;
         }
-    size_t need = carve(h, nullptr, nullptr, nullptr);
+    const bool dev32 = params->precision == FELBM_FP32_DEV;
+    size_t need = carve(h, dev32, nullptr, nullptr, nullptr);
     if (!d_workspace || workspace_bytes < need || (reinterpret_cast<uintptr_t>(d_workspace) & 255)) {
         set_error("felbm_init: workspace missing, not 256-byte aligned or smaller than felbm_workspace_bytes");
         return FELBM_ERR_WORKSPACE;
@@ -776,7 +1007,8 @@ int felbm_init(const felbm_mesh* mesh, const felbm_params* params, const double*
     st->hm = h;
     st->prm = *params;
     st->stream = static_cast<cudaStream_t>(stream);
-    carve(h, d_workspace, &st->dm, &st->buf);
+    st->dev32 = dev32;
+    carve(h, dev32, d_workspace, &st->dm, &st->buf);
     Phys& ph = st->phys;
     ph.dt = params->dt;
     ph.tau_l = params->tau_l;
@@ -787,9 +1019,19 @@ int felbm_init(const felbm_mesh* mesh, const felbm_params* params, const double*
     ph.beta = params->beta;
     ph.mobility = params->mobility;
     for (int k = 0; k < FELBM_MAX_WALL_IDS; ++k) ph.phi_c[k] = params->phi_c[k];
+    ph.dt_f = (float)params->dt;
+    ph.dt3_f = (float)(params->dt / 3.0);
+    ph.dt2h_f = (float)(0.5 * params->dt * params->dt);
+    ph.inv_tau_l_f = (float)(1.0 / params->tau_l);
+    ph.inv_tau_v_f = (float)(1.0 / params->tau_v);
+    ph.rho_v_f = (float)params->rho_v;
+    ph.drho_f = (float)(params->rho_l - params->rho_v);
+    ph.mobility_f = (float)params->mobility;
 
     // Chebyshev coefficients for the spectrum [1/4, 1] of m^{-1} M11
-    st->sweeps = params->solver_iters ? params->solver_iters : 32;
+    st->mode = params->solver_mode;
+    st->sweeps = params->solver_iters ? params->solver_iters : (st->mode == FELBM_SOLVER_FP64 ? 32 : 14);
+    st->rounds = st->mode == FELBM_SOLVER_FP64 ? 1 : (params->solver_rounds ? params->solver_rounds : (dev32 ? 1 : 3));
     const double lmin = 0.25, lmax = 1.0;
     const double theta = 0.5 * (lmax + lmin), delta = 0.5 * (lmax - lmin), sigma1 = theta / delta;
     st->inv_theta = 1.0 / theta;
@@ -806,9 +1048,11 @@ int felbm_init(const felbm_mesh* mesh, const felbm_params* params, const double*
     // host-side derived tables
     const double scale = params->lap_mode == FELBM_LAP_PAPER ? 1.0 : 2.0 / 3.0;
     std::vector<double> inv_vol(h.N), inv_lumped(h.N), lval(h.row_ptr[h.N]);
+    std::vector<float> inv_lumped32(h.N), mval32(h.mass.begin(), h.mass.end());
     for (int32_t i = 0; i < h.N; ++i) {
         inv_vol[i] = 1.0 / (scale * h.patch[i]);
         inv_lumped[i] = 1.0 / h.lumped[i];
+        inv_lumped32[i] = (float)inv_lumped[i];
         for (int32_t k = h.row_ptr[i]; k < h.row_ptr[i + 1]; ++k) lval[k] = -2.0 * h.stiff[k] * inv_vol[i];
     }
     auto pad_tri = [&](const std::vector<int32_t>& src, int rows) {
@@ -827,6 +1071,8 @@ int felbm_init(const felbm_mesh* mesh, const felbm_params* params, const double*
     };
     std::vector<int32_t> tri_p = pad_tri(h.tri, 3), nbr_p = pad_tri(h.nbr, 3);
     std::vector<double> grad_p = pad_trid(h.grad, 6), area_p = pad_trid(h.area, 1);
+    std::vector<float> grad32_p(grad_p.begin(), grad_p.end()), area32_p(area_p.begin(), area_p.end());
+    std::vector<float> inc_bx32(h.inc_bx.begin(), h.inc_bx.end()), inc_by32(h.inc_by.begin(), h.inc_by.end());
     cudaStream_t s = st->stream;
     const DevMesh& d = st->dm;
     auto fail = [&](cudaError_t e, const char* what) {
@@ -840,18 +1086,24 @@ int felbm_init(const felbm_mesh* mesh, const felbm_params* params, const double*
     UP(d.tri, tri_p);
     UP(d.area, area_p);
     UP(d.grad, grad_p);
+    UP(d.grad32, grad32_p);
+    UP(d.area32, area32_p);
     UP(d.nbr, nbr_p);
     UP(d.row_ptr, h.row_ptr);
     UP(d.col, h.col);
     UP(d.mval, h.mass);
     UP(d.lval, lval);
     UP(d.inv_lumped, inv_lumped);
+    UP(d.mval32, mval32);
+    UP(d.inv_lumped32, inv_lumped32);
     UP(d.lumped, h.lumped);
     UP(d.inv_vol, inv_vol);
     UP(d.inc_ptr, h.inc_ptr);
     UP(d.inc_tri, h.inc_tri);
     UP(d.inc_bx, h.inc_bx);
     UP(d.inc_by, h.inc_by);
+    UP(d.inc_bx32, inc_bx32);
+    UP(d.inc_by32, inc_by32);
     UP(d.wall_a, h.wall_a);
     UP(d.wall_b, h.wall_b);
     UP(d.wall_id, h.wall_id);
@@ -868,7 +1120,10 @@ int felbm_init(const felbm_mesh* mesh, const felbm_params* params, const double*
     if (e != cudaSuccess) return fail(e, "felbm_init: upload");
     e = cudaMemcpyAsync(st->buf.stage, C0, sizeof(double) * h.N, cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return fail(e, "felbm_init: upload C0");
-    k_init_state<<<grid_for(h.N, kBlock), kBlock, 0, s>>>(st->dm, st->buf.stage, st->buf.psi);
+    if (dev32)
+        k_init_dev32<<<grid_for(h.N, kBlock), kBlock, 0, s>>>(st->dm, st->buf, st->buf.stage);
+    else
+        k_init_state<<<grid_for(h.N, kBlock), kBlock, 0, s>>>(st->dm, st->buf.stage, st->buf.psi);
     e = cudaGetLastError();
     if (e != cudaSuccess) return fail(e, "felbm_init: launch");
     e = cudaStreamSynchronize(s);
@@ -949,8 +1204,8 @@ int felbm_timing_get(felbm_state* st, felbm_step_timing* out) {
     out->rhs_ms = t[4];
     out->solve_ms = t[5];
     out->total_ms = t[0] + t[1] + t[2] + t[3] + t[4] + t[5];
-    out->solve_launches = st->sweeps - 1;
-    out->launches = 5 + st->sweeps - 1;
+    out->solve_launches = solve_launches(st);
+    out->launches = step_launches(st);
     return FELBM_OK;
 }
 
@@ -971,9 +1226,12 @@ int felbm_diagnostics(felbm_state* st, const felbm_diag_request* req, felbm_diag
         rq.band = req->band;
     }
     cudaStream_t s = st->stream;
-    k_diag_nodes<<<kDiagBlocks, kBlock, 0, s>>>(st->dm, st->phys, st->buf, rq);
+    if (st->dev32)
+        k_diag_nodes<true><<<kDiagBlocks, kBlock, 0, s>>>(st->dm, st->phys, st->buf, rq);
+    else
+        k_diag_nodes<false><<<kDiagBlocks, kBlock, 0, s>>>(st->dm, st->phys, st->buf, rq);
     k_diag_edges<<<kDiagBlocks, kBlock, 0, s>>>(st->dm, st->buf, rq);
-    k_diag_final<<<1, 32, 0, s>>>(st->buf);
+    k_diag_final<<<1, 13 * 32, 0, s>>>(st->buf);
     FELBM_CUDA(cudaGetLastError());
     double v[kDiagSlots];
     FELBM_CUDA(cudaMemcpyAsync(v, st->buf.diag_out, sizeof v, cudaMemcpyDeviceToHost, s));
@@ -1028,7 +1286,10 @@ int felbm_get_state(felbm_state* st, double* g, double* h) {
     }
     cudaStream_t s = st->stream;
     const int N = st->dm.N;
-    k_gather_out<<<grid_for(N, kBlock), kBlock, 0, s>>>(st->dm, st->buf.psi, st->buf.stage, 18);
+    if (st->dev32)
+        k_dev32_to_full<<<grid_for(N, kBlock), kBlock, 0, s>>>(st->dm, st->phys, st->buf, st->buf.stage);
+    else
+        k_gather_out<<<grid_for(N, kBlock), kBlock, 0, s>>>(st->dm, st->buf.psi, st->buf.stage, 18);
     FELBM_CUDA(cudaGetLastError());
     FELBM_CUDA(cudaMemcpyAsync(g, st->buf.stage, sizeof(double) * 9 * N, cudaMemcpyDeviceToHost, s));
     FELBM_CUDA(cudaMemcpyAsync(h, st->buf.stage + (size_t)9 * N, sizeof(double) * 9 * N, cudaMemcpyDeviceToHost, s));
@@ -1045,7 +1306,10 @@ int felbm_set_state(felbm_state* st, const double* g, const double* h) {
     const int N = st->dm.N;
     FELBM_CUDA(cudaMemcpyAsync(st->buf.stage, g, sizeof(double) * 9 * N, cudaMemcpyHostToDevice, s));
     FELBM_CUDA(cudaMemcpyAsync(st->buf.stage + (size_t)9 * N, h, sizeof(double) * 9 * N, cudaMemcpyHostToDevice, s));
-    k_scatter_in<<<grid_for(N, kBlock), kBlock, 0, s>>>(st->dm, st->buf.stage, st->buf.psi, 18);
+    if (st->dev32)
+        k_full_to_dev32<<<grid_for(N, kBlock), kBlock, 0, s>>>(st->dm, st->phys, st->buf, st->buf.stage);
+    else
+        k_scatter_in<<<grid_for(N, kBlock), kBlock, 0, s>>>(st->dm, st->buf.stage, st->buf.psi, 18);
     FELBM_CUDA(cudaGetLastError());
     FELBM_CUDA(cudaStreamSynchronize(s));
     return FELBM_OK;
@@ -1058,10 +1322,26 @@ int felbm_get_fields(felbm_state* st, double* C, double* p, double* ux, double* 
     }
     cudaStream_t s = st->stream;
     const DevMesh& m = st->dm;
+    double* outs[5] = {C, p, ux, uy, mu};
+    if (st->dev32) {
+        k_mu32<<<grid_for(m.N, kBlock), kBlock, 0, s>>>(m, st->phys, st->buf);
+        FELBM_CUDA(cudaGetLastError());
+        const float* srcs[5] = {nullptr, st->buf.p32, st->buf.ux32, st->buf.uy32, st->buf.mu32};
+        for (int k = 0; k < 5; ++k) {
+            if (!outs[k]) continue;
+            if (k == 0)
+                k_gather_out<<<grid_for(m.N, kBlock), kBlock, 0, s>>>(m, st->buf.C, st->buf.stage, 1);
+            else
+                k_gather_out_f<<<grid_for(m.N, kBlock), kBlock, 0, s>>>(m, srcs[k], st->buf.stage);
+            FELBM_CUDA(cudaGetLastError());
+            FELBM_CUDA(cudaMemcpyAsync(outs[k], st->buf.stage, sizeof(double) * m.N, cudaMemcpyDeviceToHost, s));
+            FELBM_CUDA(cudaStreamSynchronize(s));
+        }
+        return FELBM_OK;
+    }
     k_collide<<<grid_for(m.N, kBlock), kBlock, 0, s>>>(m, st->phys, st->buf, 0);
     k_mu<<<grid_for(m.N, kBlock), kBlock, 0, s>>>(m, st->phys, st->buf);
     FELBM_CUDA(cudaGetLastError());
-    double* outs[5] = {C, p, ux, uy, mu};
     double* srcs[5] = {st->buf.C, st->buf.p, st->buf.ux, st->buf.uy, st->buf.mu};
     for (int k = 0; k < 5; ++k) {
         if (!outs[k]) continue;
@@ -1084,14 +1364,11 @@ int felbm_mass_solve(felbm_state* st, const double* B, double* X, int32_t k) {
     FELBM_CUDA(cudaMemcpyAsync(b.stage, B, sizeof(double) * k * m.N, cudaMemcpyHostToDevice, s));
     k_scatter_in<<<grid_for(m.N, kBlock), kBlock, 0, s>>>(m, b.stage, b.rhs, k);
     if (k < 18) k_zero_rows<<<grid_for(m.N, kBlock), kBlock, 0, s>>>(m, b.rhs, k, 18);
-    k_cheb_start<<<grid_for(m.N, kBlock), kBlock, 0, s>>>(m, b, st->inv_theta);
-    const double* result = b.x1;
-    for (int it = 1; it < st->sweeps; ++it) {
-        const double* cur = (it & 1) ? b.x1 : b.x0;
-        double* prev = (it & 1) ? b.x0 : b.x1;
-        k_cheb<<<grid_for(m.N, 128), 128, 0, s>>>(m, b, cur, prev, st->cheb_a[it], st->cheb_c[it], it == 1, 0);
-        result = prev;
-    }
+    if (st->mode == FELBM_SOLVER_FP64)
+        k_cheb_start<false><<<grid_for(m.N, kBlock), kBlock, 0, s>>>(m, b, st->inv_theta);
+    else
+        k_cheb_start<true><<<grid_for(m.N, kBlock), kBlock, 0, s>>>(m, b, st->inv_theta);
+    const double* result = enqueue_solve(st, b, s, false);
     k_gather_out<<<grid_for(m.N, kBlock), kBlock, 0, s>>>(m, result, b.stage, k);
     FELBM_CUDA(cudaGetLastError());
     FELBM_CUDA(cudaMemcpyAsync(X, b.stage, sizeof(double) * k * m.N, cudaMemcpyDeviceToHost, s));

@@ -17,7 +17,8 @@ from . import build as _build
 
 MAX_WALL_IDS = 8
 LAP_CONSISTENT, LAP_PAPER = 0, 1
-FP64 = 0
+FP64, FP32_DEV = 0, 1
+SOLVER_MIXED, SOLVER_FP64 = 0, 1
 
 _ERRORS = {
     -1: "invalid argument", -2: "bad mesh", -3: "CUDA error", -4: "workspace",
@@ -37,7 +38,8 @@ class Params(ctypes.Structure):
                 ("kappa", ctypes.c_double), ("beta", ctypes.c_double),
                 ("mobility", ctypes.c_double), ("phi_c", ctypes.c_double * MAX_WALL_IDS),
                 ("n_wall_ids", ctypes.c_int32), ("lap_mode", ctypes.c_int32),
-                ("precision", ctypes.c_int32), ("solver_iters", ctypes.c_int32)]
+                ("precision", ctypes.c_int32), ("solver_mode", ctypes.c_int32),
+                ("solver_iters", ctypes.c_int32), ("solver_rounds", ctypes.c_int32)]
 
 
 class MeshInfo(ctypes.Structure):
@@ -138,7 +140,8 @@ def _ptr(a):
     return a.data_ptr()
 
 
-def params_derive(phys, lap_mode=LAP_CONSISTENT, solver_iters=0, precision=FP64):
+def params_derive(phys, lap_mode=LAP_CONSISTENT, solver_iters=0, precision=FP64,
+                  solver_mode=SOLVER_MIXED, solver_rounds=0):
     """felbm_params from a physical description (sigma, xi, contact angles in
     degrees, dt, tau_l, tau_v, rho_l, rho_v, mobility)."""
     p = Params()
@@ -151,7 +154,9 @@ def params_derive(phys, lap_mode=LAP_CONSISTENT, solver_iters=0, precision=FP64)
                                      int(th.size), ctypes.byref(p)))
     p.lap_mode = lap_mode
     p.precision = precision
+    p.solver_mode = solver_mode
     p.solver_iters = solver_iters
+    p.solver_rounds = solver_rounds
     return p
 
 

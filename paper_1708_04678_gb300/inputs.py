@@ -179,10 +179,12 @@ def droplet_C0(xy, centre, R, xi, period=(0.0, 0.0)):
 # Time steps: the Taylor-Galerkin streaming step is explicit, and dt = 0.5
 # (h = 1) exceeds its stability limit on these meshes (noisy uniform states
 # grow at dt >= 0.35 on 2-triangle cells with 0.2h jitter, and at dt >= 0.15
-# on the 4-triangle cells with 0.25h jitter).  The workloads therefore use
-# dt = 0.25 on 2-triangle meshes and dt = 0.1 on the 4-triangle mesh.
+# on small 4-triangle meshes with 0.25h jitter; the 256x256 4-triangle mesh,
+# whose jitter leaves slivers of area 0.004 h^2, diverges at dt = 0.08 and is
+# stable at dt <= 0.06).  The workloads therefore use dt = 0.25 on 2-triangle
+# meshes and dt = 0.05 on the 4-triangle meshes.
 DT_GRID = 0.25
-DT_CROSS = 0.1
+DT_CROSS = 0.05
 
 
 def _phys(**kw):
@@ -222,7 +224,7 @@ def small_sessile(nx=32, ny=16, seed=11, R=7.0, theta=90.0, jitter=0.2, steps=50
 def free_droplet_256(seed=1, n=256, R=48.0, steps=20000):
     """Static free droplet in a doubly periodic n x n box meshed with 4
     triangles per cell (131,585 grid points at n=256), jitter 0.25h, R=48,
-    xi 4, density ratio 100, tau 0.6, sigma 0.005, M 0.02, dt 0.1."""
+    xi 4, density ratio 100, tau 0.6, sigma 0.005, M 0.02, dt 0.05."""
     mesh = cross_mesh(n, n, 0.25, seed)
     centre = (n / 2.0, n / 2.0)
     phys = _phys(dt=DT_CROSS, rho_v=0.01, tau_l=0.6, tau_v=0.6, sigma=0.005, theta_deg=())

@@ -21,9 +21,11 @@ def oracle_sim(w, lap="consistent"):
     return OracleSim(om, params_from_physical(w["phys"], lap), w["C0"])
 
 
-def gpu_state(w, lap="consistent", solver_iters=0, stream=None):
+def gpu_state(w, lap="consistent", solver_iters=0, stream=None, solver_mode=F.SOLVER_MIXED,
+              precision=F.FP64):
     mesh = F.Mesh.from_dict(w["mesh"])
-    prm = F.params_derive(w["phys"], LAP[lap], solver_iters=solver_iters)
+    prm = F.params_derive(w["phys"], LAP[lap], solver_iters=solver_iters, solver_mode=solver_mode,
+                          precision=precision)
     return F.State(mesh, prm, w["C0"], stream=stream)
 
 

@@ -1,0 +1,106 @@
+"""FP32 deviation storage (FELBM_FP32_DEV) against the FP64 oracle and the FP64
+GPU path.
+
+Short runs compare the state with the oracle at FP32 level.  Long runs hold
+the FP32 form to what the method's users measure: contact angle within 0.5
+degree, relative mass drift below 1e-6, and spurious currents / Laplace
+pressure close to the FP64 run.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_1708_04678_gb300 import felbm as F
+from paper_1708_04678_gb300 import inputs as I
+from parity_util import compare_states, gpu_state, oracle_sim, rel_err
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1708_04678_gb300 import build
+    build.build()
+
+
+def _dev(w, **kw):
+    return gpu_state(w, precision=F.FP32_DEV, **kw)
+
+
+def test_state_roundtrip():
+    w = I.small_sessile(nx=40, ny=20, R=9.0, theta=60.0)
+    a = gpu_state(w)
+    a.step(30)
+    g, h = a.get_state()
+    b = _dev(w)
+    b.set_state(g, h)
+    g2, h2 = b.get_state()
+    assert rel_err(g2, g) < 1e-6
+    assert rel_err(h2, h) < 1e-6
+    f = b.get_fields()
+    assert rel_err(f["C"], h.sum(0)) < 1e-14        # C is kept in FP64
+
+
+@pytest.mark.parametrize("name", ["sessile60", "free_droplet", "rough_wall"])
+def test_steps_match_oracle_at_fp32_level(name):
+    w = {"sessile60": lambda: I.small_sessile(nx=40, ny=20, R=9.0, theta=60.0),
+         "free_droplet": lambda: I.small_free_droplet(n=24, R=6.0),
+         "rough_wall": lambda: I.rough_wall_droplet(width=192, height=64, rows=49, R=20.0)}[name]()
+    osim = oracle_sim(w)
+    gst = _dev(w)
+    osim.step(20)
+    gst.step(20)
+    err = compare_states(osim, gst)
+    assert err["C"] < 1e-6, err
+    assert err["h"] < 1e-5 and err["g"] < 1e-3, err
+
+
+def test_static_interface_balance_fp32():
+    """kappa = beta = 0, u = p = 0: C must stay put (Sec. II.C balance)."""
+    m = I.cross_mesh(32, 32, 0.2, 7)
+    rng = np.random.default_rng(4)
+    C0 = rng.uniform(0, 1, len(m["xy"]))
+    phys = dict(dt=0.1, tau_l=0.8, tau_v=0.8, rho_l=1.0, rho_v=0.1, sigma=0.01, xi=4.0,
+                mobility=0.02, theta_deg=())
+    prm = F.params_derive(phys, precision=F.FP32_DEV)
+    prm.kappa = 0.0
+    prm.beta = 0.0
+    st = F.State(F.Mesh.from_dict(m), prm, C0)
+    st.step(50)
+    f = st.get_fields()
+    assert np.abs(f["C"] - C0).max() < 1e-6
+    assert np.abs(f["ux"]).max() < 1e-6
+
+
+@pytest.mark.parametrize("theta", [60.0, 120.0])
+def test_sessile_fp32_matches_fp64_contact_angle_and_mass(theta):
+    w = I.small_sessile(nx=64, ny=32, seed=0, R=12.0, theta=theta, steps=4000)
+    a = gpu_state(w)
+    b = _dev(w)
+    a.step(w["steps"])
+    b.step(w["steps"])
+    da = a.diagnostics(w["centre"], w["R"], 4.0, 0)
+    db = b.diagnostics(w["centre"], w["R"], 4.0, 0)
+    assert abs(da["theta_deg"] - db["theta_deg"]) < 0.5, (da["theta_deg"], db["theta_deg"])
+    assert abs(db["mass_drift_rel"]) < 1e-6, db["mass_drift_rel"]
+    assert abs(da["mass_drift_rel"]) < 1e-12
+    assert math.isclose(da["max_u"], db["max_u"], rel_tol=0.05, abs_tol=1e-5)
+
+
+def test_free_droplet_256_fp32_spurious_currents_and_laplace():
+    """The 256x256 free droplet: 1,000 steps in both precisions."""
+    w = I.free_droplet_256()
+    a = gpu_state(w)
+    b = _dev(w)
+    a.step(1000)
+    b.step(1000)
+    da = a.diagnostics(w["centre"], w["R"], 4.0)
+    db = b.diagnostics(w["centre"], w["R"], 4.0)
+    assert db["status"] == 0
+    assert abs(db["mass_drift_rel"]) < 1e-6
+    assert math.isclose(da["delta_p"], db["delta_p"], rel_tol=0.02)
+    assert math.isclose(da["max_u"], db["max_u"], rel_tol=0.05, abs_tol=1e-6)

@@ -34,10 +34,11 @@ def _rough_small(theta=60.0):
     return I.rough_wall_droplet(width=192, height=64, rows=49, R=20.0, theta=theta, steps=50)
 
 
-def test_mass_solve_matches_oracle_pcg():
+@pytest.mark.parametrize("mode", [F.SOLVER_MIXED, F.SOLVER_FP64])
+def test_mass_solve_matches_oracle_pcg(mode):
     w = I.sessile_droplet_64x32()
     osim = oracle_sim(w)
-    gst = gpu_state(w)
+    gst = gpu_state(w, solver_mode=mode)
     rng = np.random.default_rng(0)
     B = rng.standard_normal((18, gst.N))
     X = gst.mass_solve(B)
@@ -89,6 +90,17 @@ def test_multi_step(name, steps):
     gst = gpu_state(w, lap)
     osim.step(steps)
     gst.step(steps)
+    err = compare_states(osim, gst)
+    assert max(err.values()) < TOL, err
+
+
+@pytest.mark.parametrize("mode", [F.SOLVER_MIXED, F.SOLVER_FP64])
+def test_solver_modes_multi_step(mode):
+    w = WORKLOADS["sessile60"]()
+    osim = oracle_sim(w)
+    gst = gpu_state(w, solver_mode=mode)
+    osim.step(200)
+    gst.step(200)
     err = compare_states(osim, gst)
     assert max(err.values()) < TOL, err
 
