@@ -200,6 +200,34 @@ int felbm_get_fields(felbm_state* state, double* C, double* p, double* ux, doubl
  * overlap with felbm_step on another stream.  Synchronises. */
 int felbm_mass_solve(felbm_state* state, const double* B, double* X, int32_t k);
 
+/* Capacity of the device scratch array behind felbm_mass_solve_static. */
+#define FELBM_STATIC_SCRATCH_BYTES (64u << 20)
+
+/* felbm_mass_solve without any device allocation, for callers that cannot
+ * allocate: code running where cudaMalloc is not allowed or not wanted (a
+ * host callback, a stream-ordered section that must not synchronise, a
+ * plugin whose host application owns all device memory) and that cannot
+ * lend the state's workspace either, because felbm_step may be using it.
+ * The paper has no counterpart: this is an interface convenience only.
+ *
+ * Solves M11 X = B exactly as felbm_mass_solve does (same solver, same
+ * arithmetic) but takes DEVICE pointers and keeps its iterates in one
+ * library-owned static device array of FELBM_STATIC_SCRATCH_BYTES (64 MiB)
+ * per GPU, held by every GPU that loads the library until the process
+ * exits.  Nothing is allocated and nothing is freed.
+ *  d_B, d_X  device pointers, double [k][n_nodes], caller order; 1 <= k <= 18.
+ *            X may not alias B.
+ *  Size limit: the 18-row scratch needs 648 bytes per node (padded to 64
+ *  nodes), i.e. meshes up to ~103,000 nodes; larger meshes get
+ *  FELBM_ERR_WORKSPACE before anything is enqueued.
+ * Enqueued on the state's stream; returns without synchronising.  The first
+ * call on a device looks up the array's device address (once per device, with
+ * that device made current); make that first call before any stream capture.
+ * Every call shares the one array of its device and leaves its contents
+ * behind: calls that overlap on the GPU race, so serialise them (one stream,
+ * or events).  They may overlap with felbm_step, which does not touch it. */
+int felbm_mass_solve_static(felbm_state* state, const double* d_B, double* d_X, int32_t k);
+
 /* Device time of the phases of one time step, milliseconds, from CUDA events
  * recorded inside the step's graph (instrumentation, not part of the method). */
 typedef struct felbm_step_timing {

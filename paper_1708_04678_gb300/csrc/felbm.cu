@@ -33,6 +33,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -1373,6 +1374,92 @@ int felbm_mass_solve(felbm_state* st, const double* B, double* X, int32_t k) {
     FELBM_CUDA(cudaGetLastError());
     FELBM_CUDA(cudaMemcpyAsync(X, b.stage, sizeof(double) * k * m.N, cudaMemcpyDeviceToHost, s));
     FELBM_CUDA(cudaStreamSynchronize(s));
+    return FELBM_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------- no-allocation mass solve -------
+// The iterates of felbm_mass_solve_static live here, not in any allocation.
+static __device__ __align__(256) unsigned char g_static_scratch[FELBM_STATIC_SCRATCH_BYTES];
+
+namespace felbm {
+
+static std::mutex g_static_mu;
+static void* g_static_addr[64] = {};   // device address of g_static_scratch per device ordinal
+
+// Device address of the scratch array on `device`, looked up once per device
+// with that device current (the host-side symbol is not a device address).
+static int static_scratch(int device, void** out) {
+    if (device < 0 || device >= 64) {
+        set_error("felbm_mass_solve_static: device ordinal out of range");
+        return FELBM_ERR_INVALID_ARG;
+    }
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    if (!g_static_addr[device]) {
+        int current = 0;
+        FELBM_CUDA(cudaGetDevice(&current));
+        if (current != device) FELBM_CUDA(cudaSetDevice(device));
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+        if (current != device) cudaSetDevice(current);
+        if (e != cudaSuccess) return cuda_fail(e, "felbm_mass_solve_static: cudaGetSymbolAddress");
+        g_static_addr[device] = p;
+    }
+    *out = g_static_addr[device];
+    return FELBM_OK;
+}
+
+}  // namespace felbm
+
+extern "C" {
+
+int felbm_mass_solve_static(felbm_state* st, const double* d_B, double* d_X, int32_t k) {
+    if (!st || !d_B || !d_X || k < 1 || k > 18 || d_B == d_X) {
+        set_error("felbm_mass_solve_static: invalid argument (device B, X distinct; 1 <= k <= 18)");
+        return FELBM_ERR_INVALID_ARG;
+    }
+    const DevMesh& m = st->dm;
+    // the solve's buffers: 18 rows of stride Np, 256-byte aligned pieces
+    Carver cv(nullptr);
+    const size_t rows = 18 * (size_t)m.Np;
+    cv.take<double>(rows);
+    cv.take<double>(rows);
+    cv.take<double>(rows);
+    cv.take<float>(rows);
+    cv.take<float>(rows);
+    cv.take<float>(rows);
+    if (cv.off > FELBM_STATIC_SCRATCH_BYTES) {
+        char buf[256];
+        snprintf(buf, sizeof buf,
+                 "felbm_mass_solve_static: %d nodes need %zu bytes of scratch, the static array holds %u",
+                 m.N, cv.off, (unsigned)FELBM_STATIC_SCRATCH_BYTES);
+        set_error(buf);
+        return FELBM_ERR_WORKSPACE;
+    }
+    void* base = nullptr;
+    int rc = static_scratch(st->device, &base);
+    if (rc) return rc;
+    Carver sc(base);
+    Bufs sb = st->buf;
+    sb.rhs = sc.take<double>(rows);
+    sb.x0 = sc.take<double>(rows);
+    sb.x1 = sc.take<double>(rows);
+    sb.x64 = sb.x0;
+    sb.rho64 = sb.x1;
+    sb.r32 = sc.take<float>(rows);
+    sb.e0 = sc.take<float>(rows);
+    sb.e1 = sc.take<float>(rows);
+    cudaStream_t s = st->stream;
+    k_scatter_in<<<grid_for(m.N, kBlock), kBlock, 0, s>>>(m, d_B, sb.rhs, k);
+    if (k < 18) k_zero_rows<<<grid_for(m.N, kBlock), kBlock, 0, s>>>(m, sb.rhs, k, 18);
+    if (st->mode == FELBM_SOLVER_FP64)
+        k_cheb_start<false><<<grid_for(m.N, kBlock), kBlock, 0, s>>>(m, sb, st->inv_theta);
+    else
+        k_cheb_start<true><<<grid_for(m.N, kBlock), kBlock, 0, s>>>(m, sb, st->inv_theta);
+    const double* result = enqueue_solve(st, sb, s, false);
+    k_gather_out<<<grid_for(m.N, kBlock), kBlock, 0, s>>>(m, result, d_X, k);
+    FELBM_CUDA(cudaGetLastError());
     return FELBM_OK;
 }
 

@@ -101,6 +101,7 @@ def _declare(lib):
         "felbm_set_state": (ctypes.c_int, [_P, _P, _P]),
         "felbm_get_fields": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
         "felbm_mass_solve": (ctypes.c_int, [_P, _P, _P, _I32]),
+        "felbm_mass_solve_static": (ctypes.c_int, [_P, _P, _P, _I32]),
         "felbm_timing_enable": (ctypes.c_int, [_P, _I32]),
         "felbm_timing_get": (ctypes.c_int, [_P, ctypes.POINTER(StepTiming)]),
         "felbm_state_destroy": (None, [_P]),
@@ -269,6 +270,12 @@ class State:
         X = np.empty_like(B)
         _check(lib().felbm_mass_solve(self.handle, _ptr(B), _ptr(X), k))
         return X
+
+    def mass_solve_static(self, d_B, d_X, k=None):
+        """felbm_mass_solve_static: device tensors B, X of shape (k, n_nodes),
+        float64, caller order; enqueued on the state's stream."""
+        k = d_B.shape[0] if k is None else k
+        _check(lib().felbm_mass_solve_static(self.handle, d_B.data_ptr(), d_X.data_ptr(), int(k)))
 
     def timing_enable(self, on=True):
         _check(lib().felbm_timing_enable(self.handle, 1 if on else 0))
