@@ -21,6 +21,8 @@
  *  - Streams: all device work of a state is enqueued on the cudaStream_t given
  *    to felbm_init (passed as void*; NULL = legacy default stream).  Calls
  *    that return host data synchronise that stream; felbm_step does not.
+ *  - Environment: FELBM_PDL=0 launches the solve sweeps without programmatic
+ *    dependent launch (read at felbm_init; default on).
  *  - Distribution layout on the host: double [9][n_nodes], direction-major,
  *    D2Q9 order e_0 = (0,0), e_1..e_4 = (1,0),(0,1),(-1,0),(0,-1),
  *    e_5..e_8 = (1,1),(-1,1),(-1,-1),(1,-1); weights 4/9, 1/9, 1/36.

@@ -32,8 +32,10 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
+#include <utility>
 #include <new>
 #include <string>
 #include <vector>
@@ -86,6 +88,9 @@ struct DevMesh {
     const double* lval;       // [nnz] -2 K_ij / V_i (patch Laplacian of C)
     const double* inv_lumped; // [Np]
     const float* mval32;      // [nnz] FP32 copy of the mass entries
+    int32_t ell_w;            // width of the ELL copy (max row length), 0 = none
+    const int32_t* ell_col;   // [ell_w][Np] column-major ELL copy of the pattern
+    const float* ell_val;     // [ell_w][Np] FP32 mass entries (padding: own column, 0)
     const float* inv_lumped32;// [Np]
     const double* lumped;     // [Np]
     const double* inv_vol;    // [Np] 1 / V_i
@@ -483,6 +488,69 @@ __global__ void __launch_bounds__(128) k_cheb32(DevMesh m, Phys c, Bufs b, const
     if (kFinal == kUpdateDev) dev32_update(m, c, b, i, d);
 }
 
+// Programmatic dependent launch: a sweep may be scheduled while its
+// predecessor drains; it loads its (read-only) matrix row first and waits for
+// the predecessor's results before touching them.  Both instructions are
+// no-ops for a kernel launched without the attribute.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_release() { asm volatile("griddepcontrol.launch_dependents;" :::); }
+
+// The FP32 sweep of k_cheb32 on the ELL copy of the pattern (kW entries per
+// row, padded with the own column and value 0).  Row indices and values are
+// loaded up front (coalesced, column-major); for the store variant the g and
+// h halves of a node run in two threads (blockIdx.y), doubling the threads in
+// flight for this latency-bound gather.
+template <int kFinal, int kW>
+__global__ void __launch_bounds__(128) k_sweep32(DevMesh m, Phys c, Bufs b, const float* __restrict__ cur,
+                                                 float* prev, float a, float cc, int first, int have_x64) {
+    pdl_release();
+    constexpr bool kSplit = kFinal != kUpdateDev;
+    constexpr int NQ = kSplit ? 9 : 18;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int q0 = kSplit ? 9 * (int)blockIdx.y : 0;
+    const int Np = m.Np;
+    int col[kW];
+    float val[kW];
+    if (i < m.N) {
+#pragma unroll
+        for (int k = 0; k < kW; ++k) {
+            col[k] = m.ell_col[k * Np + i];
+            val[k] = m.ell_val[k * Np + i];
+        }
+    }
+    const float s = cc * (i < m.N ? m.inv_lumped32[i] : 0.0f);
+    pdl_wait();
+    if (i >= m.N) return;
+    float acc[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) acc[q] = 0.0f;
+#pragma unroll
+    for (int k = 0; k < kW; ++k) {
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) acc[q] = fmaf(val[k], cur[(q0 + q) * Np + col[k]], acc[q]);
+    }
+    float d[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+        const int r = (q0 + q) * Np + i;
+        float xk = cur[r];
+        float xm = first ? 0.0f : prev[r];
+        float xn = xk + a * (xk - xm) + s * (b.r32[r] - acc[q]);
+        if (kFinal == kStore) {
+            prev[r] = xn;
+        } else if (kFinal == kUpdateDev) {
+            d[q] = xn;
+        } else {
+            double x = have_x64 ? b.x64[r] + (double)xn : (double)xn;
+            if (kFinal == kAddPsi)
+                b.psi[r] += x;
+            else
+                b.x64[r] = x;
+        }
+    }
+    if constexpr (kFinal == kUpdateDev) dev32_update(m, c, b, i, d);
+}
+
 // x <- x + e ; rho <- rho - M11 e (FP64) ; FP32 copy of rho and the first
 // Chebyshev iterate of the next correction, rho / (m theta).
 __global__ void __launch_bounds__(128) k_refine(DevMesh m, Bufs b, const float* __restrict__ e,
@@ -748,9 +816,19 @@ struct felbm_state {
     bool timed_step_ran = false;
     cudaEvent_t ev[7] = {};
     bool dev32 = false;   // FELBM_FP32_DEV storage
+    bool use_pdl = true;  // programmatic dependent launch between solve sweeps
 };
 
 namespace felbm {
+
+// ELL width used by the FP32 sweeps: the longest row rounded up to one of
+// the compiled widths; 0 (CSR sweeps) beyond 16.
+static int ell_width(const HostMesh& h) {
+    int w = h.max_degree;
+    for (int c : {7, 9, 12, 16})
+        if (w <= c) return c;
+    return 0;
+}
 
 // Layout of the workspace; with base == nullptr only the size is computed.
 static size_t carve(const HostMesh& h, bool dev32, void* base, DevMesh* dm, Bufs* b) {
@@ -771,6 +849,10 @@ static size_t carve(const HostMesh& h, bool dev32, void* base, DevMesh* dm, Bufs
     d.lval = cv.take<double>(nnz);
     d.inv_lumped = cv.take<double>(Np);
     d.mval32 = cv.take<float>(nnz);
+    const int ellw = ell_width(h);
+    d.ell_w = ellw;
+    d.ell_col = cv.take<int32_t>((size_t)std::max(ellw, 1) * Np);
+    d.ell_val = cv.take<float>((size_t)std::max(ellw, 1) * Np);
     d.inv_lumped32 = cv.take<float>(Np);
     d.lumped = cv.take<double>(Np);
     d.inv_vol = cv.take<double>(Np);
@@ -866,6 +948,49 @@ static cudaError_t up(const T* dst, const std::vector<T>& src, cudaStream_t s) {
 
 static unsigned grid_for(int n, int block) { return (unsigned)((n + block - 1) / block); }
 
+// Launch with or without programmatic dependent launch (PDL).
+template <typename... KArgs, typename... Args>
+static void launch_k(bool pdl, void (*kern)(KArgs...), dim3 grid, dim3 block, cudaStream_t s, Args&&... args) {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
+}
+
+// One FP32 Chebyshev sweep: the ELL kernel of the mesh's width, else CSR.
+// pdl: the previous launch on the stream is a sweep (a kernel that waits).
+template <int kFinal>
+static void launch_sweep(felbm_state* st, const Bufs& b, cudaStream_t s, const float* cur, float* prv,
+                         float a, float c, int first, int have_x64, bool pdl) {
+    const DevMesh& m = st->dm;
+    const dim3 block(128);
+    const dim3 grid(grid_for(m.N, 128), kFinal == kUpdateDev ? 1 : 2);
+    pdl = pdl && st->use_pdl;
+    switch (m.ell_w) {
+        case 7:
+            launch_k(pdl, k_sweep32<kFinal, 7>, grid, block, s, m, st->phys, b, cur, prv, a, c, first, have_x64);
+            break;
+        case 9:
+            launch_k(pdl, k_sweep32<kFinal, 9>, grid, block, s, m, st->phys, b, cur, prv, a, c, first, have_x64);
+            break;
+        case 12:
+            launch_k(pdl, k_sweep32<kFinal, 12>, grid, block, s, m, st->phys, b, cur, prv, a, c, first, have_x64);
+            break;
+        case 16:
+            launch_k(pdl, k_sweep32<kFinal, 16>, grid, block, s, m, st->phys, b, cur, prv, a, c, first, have_x64);
+            break;
+        default:
+            k_cheb32<kFinal><<<grid_for(m.N, 128), 128, 0, s>>>(m, st->phys, b, cur, prv, a, c, first, have_x64);
+    }
+}
+
 // Enqueue the mass solve for the right-hand side in b.rhs (first iterate
 // already written).  into_psi: add the increment to psi (time step); else
 // leave the solution in x1/x0 (FP64 mode, returned) or x64 (mixed mode).
@@ -894,15 +1019,15 @@ static const double* enqueue_solve(felbm_state* st, const Bufs& b, cudaStream_t 
         for (int k = 1; k < st->sweeps; ++k) {
             const float a = (float)st->cheb_a[k], c = (float)st->cheb_c[k];
             const bool last = r == st->rounds - 1 && k == st->sweeps - 1;
-            const Phys& ph = st->phys;
+            const bool pdl = k > 1;   // the previous launch is a sweep of this round
             if (!last)
-                k_cheb32<kStore><<<grid, 128, 0, s>>>(m, ph, b, cur, prv, a, c, k == 1, have_x64);
+                launch_sweep<kStore>(st, b, s, cur, prv, a, c, k == 1, have_x64, pdl);
             else if (!into_psi)
-                k_cheb32<kAddX64><<<grid, 128, 0, s>>>(m, ph, b, cur, prv, a, c, k == 1, have_x64);
+                launch_sweep<kAddX64>(st, b, s, cur, prv, a, c, k == 1, have_x64, pdl);
             else if (st->dev32)
-                k_cheb32<kUpdateDev><<<grid, 128, 0, s>>>(m, ph, b, cur, prv, a, c, k == 1, have_x64);
+                launch_sweep<kUpdateDev>(st, b, s, cur, prv, a, c, k == 1, have_x64, pdl);
             else
-                k_cheb32<kAddPsi><<<grid, 128, 0, s>>>(m, ph, b, cur, prv, a, c, k == 1, have_x64);
+                launch_sweep<kAddPsi>(st, b, s, cur, prv, a, c, k == 1, have_x64, pdl);
             std::swap(cur, prv);
         }
         if (r < st->rounds - 1) {
@@ -1050,6 +1175,18 @@ int felbm_init(const felbm_mesh* mesh, const felbm_params* params, const double*
     const double scale = params->lap_mode == FELBM_LAP_PAPER ? 1.0 : 2.0 / 3.0;
     std::vector<double> inv_vol(h.N), inv_lumped(h.N), lval(h.row_ptr[h.N]);
     std::vector<float> inv_lumped32(h.N), mval32(h.mass.begin(), h.mass.end());
+    const int ellw = st->dm.ell_w;
+    std::vector<int32_t> ell_col((size_t)std::max(ellw, 1) * st->dm.Np, 0);
+    std::vector<float> ell_val((size_t)std::max(ellw, 1) * st->dm.Np, 0.0f);
+    for (int32_t i = 0; i < h.N && ellw > 0; ++i) {
+        int32_t r0 = h.row_ptr[i], len = h.row_ptr[i + 1] - r0;
+        for (int k = 0; k < ellw; ++k) {
+            size_t at = (size_t)k * st->dm.Np + i;
+            ell_col[at] = k < len ? h.col[r0 + k] : i;
+            ell_val[at] = k < len ? (float)h.mass[r0 + k] : 0.0f;
+        }
+    }
+    if (const char* env = std::getenv("FELBM_PDL")) st->use_pdl = std::atoi(env) != 0;
     for (int32_t i = 0; i < h.N; ++i) {
         inv_vol[i] = 1.0 / (scale * h.patch[i]);
         inv_lumped[i] = 1.0 / h.lumped[i];
@@ -1096,6 +1233,8 @@ int felbm_init(const felbm_mesh* mesh, const felbm_params* params, const double*
     UP(d.lval, lval);
     UP(d.inv_lumped, inv_lumped);
     UP(d.mval32, mval32);
+    UP(d.ell_col, ell_col);
+    UP(d.ell_val, ell_val);
     UP(d.inv_lumped32, inv_lumped32);
     UP(d.lumped, h.lumped);
     UP(d.inv_vol, inv_vol);
