@@ -45,7 +45,7 @@ extern "C" {
 #define FELBM_ERR_NONFINITE (-5)    /* NaN or Inf found in the state */
 #define FELBM_ERR_UNSUPPORTED (-6)  /* option not available in this build */
 
-#define FELBM_MAX_WALL_IDS 8
+#define FELBM_MAX_WALL_IDS 256
 
 /* Patch Laplacian of C (eqn:lapl_int_mp): V = 2/3 |patch| (equals the lumped
  * P1 Laplacian) or V = |patch| (the literal patch area). */
@@ -103,6 +103,7 @@ typedef struct felbm_state felbm_state;
 
 typedef struct felbm_mesh_info {
     int32_t n_nodes, n_tri, n_wall_edges;
+    int32_t n_groups;         /* connected components (independent droplets of a batch) */
     int32_t nnz;              /* entries of the node-node sparsity pattern */
     int32_t max_degree;       /* largest row of that pattern */
     int32_t bandwidth;        /* after reverse Cuthill-McKee */
@@ -157,6 +158,36 @@ int felbm_mesh_create(const double* xy, int32_t n_nodes, const int32_t* tri, int
                       const int32_t* wall_edges, const int32_t* wall_id, int32_t n_wall_edges,
                       double period_x, double period_y, felbm_mesh** out);
 int felbm_mesh_info_get(const felbm_mesh* mesh, felbm_mesh_info* out);
+
+/* One member mesh of a batch: the arguments of felbm_mesh_create. */
+typedef struct felbm_mesh_desc {
+    const double* xy;
+    int32_t n_nodes;
+    const int32_t* tri;
+    int32_t n_tri;
+    const int32_t* wall_edges;
+    const int32_t* wall_id;
+    int32_t n_wall_edges;
+    double period_x, period_y;
+} felbm_mesh_desc;
+
+/* Merge independent meshes into one mesh (each keeps its own periodic
+ * lengths; node ids of member k are offset by the node counts of members
+ * 0..k-1; wall ids are used as given, so give each member its own ids to
+ * give it its own contact angle).  Same validation and errors as
+ * felbm_mesh_create.  Every kernel of felbm_step then advances all members in
+ * the same launches; felbm_diagnostics_groups reports them one by one. */
+int felbm_mesh_create_batch(int32_t n_meshes, const felbm_mesh_desc* meshes, felbm_mesh** out);
+
+/* Batches.  A mesh may consist of several connected components -- e.g. many
+ * independent droplet domains concatenated into one node/triangle list, each
+ * with its own wall ids (and so its own contact angle).  felbm_step advances
+ * all of them in the same kernel launches.  The components are the "groups",
+ * numbered by their lowest caller node id (so concatenating meshes in order
+ * numbers them in that order).  Node ranges of each group, caller order:
+ * group_first_node[g] = lowest caller id of group g; sizes in group_nodes.
+ * Either pointer may be NULL; arrays hold n_groups entries. */
+int felbm_mesh_groups(const felbm_mesh* mesh, int32_t* group_first_node, int32_t* group_nodes);
 void felbm_mesh_destroy(felbm_mesh* mesh);
 
 /* Bytes of device workspace a state of this mesh and these params needs. */
@@ -184,6 +215,38 @@ int felbm_step(felbm_state* state, int32_t n_steps);
  * Synchronises the stream.  Returns FELBM_ERR_NONFINITE (and fills *out) if
  * the state holds a NaN or Inf. */
 int felbm_diagnostics(felbm_state* state, const felbm_diag_request* req, felbm_diag* out);
+
+/* Batch schedule (FELBM_FP32_DEV states): members (groups) of at most
+ * cta_max_nodes nodes each run in ONE thread block that performs the whole
+ * time step with block-level barriers only (no kernel boundaries), on a side
+ * branch of the step's CUDA graph; the larger members run the tiled kernels
+ * meanwhile.  0 = tiled kernels for every member (default).  The step graph
+ * is rebuilt at the next felbm_step.  Results do not depend on the schedule. */
+int felbm_batch_schedule(felbm_state* state, int32_t cta_max_nodes);
+
+typedef struct felbm_tune_result {
+    int32_t cta_max_nodes;   /* chosen threshold (0 = tiled only) */
+    int32_t n_candidates;
+    int32_t candidates[16];  /* thresholds timed */
+    float step_ms[16];       /* mean device time of one step for each */
+} felbm_tune_result;
+
+/* Autotuner of the batch schedule: times `trials` steps (after one warm-up
+ * step) for each distinct split of the members -- tiled only, and CTA per
+ * member up to 2^11 .. 2^17 nodes -- and keeps the fastest.  The state (and
+ * the step count) is saved before and restored after, so the simulation is
+ * unchanged.  Synchronises.  FP64 states and one-member meshes keep the
+ * tiled schedule. */
+int felbm_autotune(felbm_state* state, int32_t trials, felbm_tune_result* out);
+
+/* Diagnostics per group (see felbm_mesh_groups): out[g] for g < n_groups, each
+ * reduced over its own nodes, triangles and wall edges in one CTA per group
+ * (deterministic).  reqs: NULL or n_groups requests (band, substrate wall id
+ * of each group).  mass0 / mass_drift_rel are relative to the group's mass
+ * at felbm_init.  Synchronises.  Returns FELBM_ERR_NONFINITE if any group
+ * holds a NaN or Inf (all of out is filled). */
+int felbm_diagnostics_groups(felbm_state* state, const felbm_diag_request* reqs, int32_t n_groups,
+                             felbm_diag* out);
 
 /* Copy the distributions out / in: g, h double [9][n_nodes] host, caller order.
  * Pinned host memory makes the copies asynchronous DMA.  Both synchronise. */

@@ -103,6 +103,7 @@ struct DevMesh {
     const int32_t* wall_a;    // [E]
     const int32_t* wall_b;
     const int32_t* wall_id;
+    const double* wall_phi;   // [E] wetting potential phi_c of the edge's wall id
     const double* wall_len;
     const double* wall_nx;
     const double* wall_ny;
@@ -116,7 +117,6 @@ struct DevMesh {
 
 struct Phys {
     double dt, tau_l, tau_v, rho_l, rho_v, kappa, beta, mobility;
-    double phi_c[FELBM_MAX_WALL_IDS];
     // FP32 copies, rounded once on the host
     float dt_f, dt3_f, dt2h_f, inv_tau_l_f, inv_tau_v_f, rho_v_f, drho_f, mobility_f;
 };
@@ -218,7 +218,7 @@ __global__ void __launch_bounds__(kBlock) k_mu(DevMesh m, Phys c, Bufs b) {
         int e = m.winc_edge[k];
         double Ca = b.C[m.wall_a[e]], Cb = b.C[m.wall_b[e]];
         double s = 0.5 * (Ca + Cb) - (Ca * Ca + Ca * Cb + Cb * Cb) * (1.0 / 3.0);
-        wall -= c.phi_c[m.wall_id[e]] * m.wall_len[e] * s;
+        wall -= m.wall_phi[e] * m.wall_len[e] * s;
     }
     double C = b.C[i];
     b.mu[i] = 2.0 * c.beta * C * (C - 1.0) * (2.0 * C - 1.0) - (c.kappa * lap + wall * m.inv_vol[i]);
@@ -660,60 +660,93 @@ __device__ void block_reduce_store(double (&s)[NS], double (&mx)[NM], double* ou
     }
 }
 
+// Per-node contributions (slots 0..9 sums, one max); writes the node's C.
+template <bool kDev32>
+__device__ __forceinline__ void diag_node(const DevMesh& m, const Phys& c, const Bufs& b, const DiagReq& rq,
+                                          int i, double (&s)[10], double (&mx)[1]) {
+    const int Np = m.Np;
+    double C = 0, p = 0, ux, uy, rho;
+    if (kDev32) {
+        C = b.C[i];
+        p = b.p32[i];
+        ux = b.ux32[i];
+        uy = b.uy32[i];
+        rho = c.rho_v + C * (c.rho_l - c.rho_v);
+        float dsum = 0.0f;
+        for (int q = 0; q < 18; ++q) dsum += b.dpsi[q * Np + i];
+        if (!isfinite(dsum)) p = dsum;   // non-finite deviations are reported too
+    } else {
+        double g[9];
+#pragma unroll
+        for (int q = 0; q < 9; ++q) {
+            g[q] = b.psi[q * Np + i];
+            p += g[q];
+            C += b.psi[(9 + q) * Np + i];
+        }
+        double mxm = (g[1] - g[3]) + (g[5] - g[6]) + (g[8] - g[7]);
+        double mym = (g[2] - g[4]) + (g[5] + g[6]) - (g[7] + g[8]);
+        rho = c.rho_v + C * (c.rho_l - c.rho_v);
+        ux = 3.0 * mxm / rho;
+        uy = 3.0 * mym / rho;
+    }
+    double uu = ux * ux + uy * uy;
+    double w = m.lumped[i];
+    b.Cdiag[i] = C;
+    if (!isfinite(C) || !isfinite(p) || !isfinite(uu)) s[9] += 1.0;
+    s[0] += w * C;
+    s[1] += rho * uu;
+    if (rq.use_band) {
+        double dx = min_image(m.x[i] - rq.cx, rq.period_x), dy = min_image(m.y[i] - rq.cy, rq.period_y);
+        double r = sqrt(dx * dx + dy * dy);
+        if (fabs(r - rq.R) <= rq.band) {
+            s[2] += w;
+            s[3] += w * rho * uu;
+        }
+    }
+    if (C >= 0.95) {
+        s[4] += w;
+        s[5] += w * p;
+    }
+    if (C <= 0.05) {
+        s[6] += w;
+        s[7] += w * p;
+    }
+    mx[0] = fmax(mx[0], uu);
+}
+
+// Wetted length of a substrate wall edge (C linear along it).
+__device__ __forceinline__ void diag_wall(const DevMesh& m, const Bufs& b, const DiagReq& rq, int e, double& wet) {
+    if (m.wall_id[e] != rq.substrate) return;
+    double Ca = b.Cdiag[m.wall_a[e]], Cb = b.Cdiag[m.wall_b[e]], L = m.wall_len[e];
+    if (Ca >= 0.5 && Cb >= 0.5)
+        wet += L;
+    else if (Ca >= 0.5 || Cb >= 0.5) {
+        double hi = fmax(Ca, Cb), lo = fmin(Ca, Cb);
+        wet += L * (hi - 0.5) / (hi - lo);
+    }
+}
+
+// Highest crossing of the C = 1/2 contour on the edges of a triangle.
+__device__ __forceinline__ void diag_tri(const DevMesh& m, const Bufs& b, const DiagReq& rq, int t, double& ymax) {
+    const int Tp = m.Tp;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        int ia = m.tri[((k + 1) % 3) * Tp + t], ic = m.tri[((k + 2) % 3) * Tp + t];
+        double Ca = b.Cdiag[ia], Cc = b.Cdiag[ic];
+        if ((Ca >= 0.5) != (Cc >= 0.5)) {
+            double tt = (0.5 - Ca) / (Cc - Ca);
+            double dy = min_image(m.y[ic] - m.y[ia], rq.period_y);
+            ymax = fmax(ymax, m.y[ia] + tt * dy);
+        }
+    }
+}
+
 template <bool kDev32>
 __global__ void __launch_bounds__(kBlock) k_diag_nodes(DevMesh m, Phys c, Bufs b, DiagReq rq) {
     double s[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
     double mx[1] = {0.0};
-    const int Np = m.Np;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m.N; i += gridDim.x * blockDim.x) {
-        double C = 0, p = 0, ux, uy, rho;
-        if (kDev32) {
-            C = b.C[i];
-            p = b.p32[i];
-            ux = b.ux32[i];
-            uy = b.uy32[i];
-            rho = c.rho_v + C * (c.rho_l - c.rho_v);
-            float dsum = 0.0f;
-            for (int q = 0; q < 18; ++q) dsum += b.dpsi[q * Np + i];
-            if (!isfinite(dsum)) p = dsum;   // non-finite deviations are reported too
-        } else {
-            double g[9];
-#pragma unroll
-            for (int q = 0; q < 9; ++q) {
-                g[q] = b.psi[q * Np + i];
-                p += g[q];
-                C += b.psi[(9 + q) * Np + i];
-            }
-            double mxm = (g[1] - g[3]) + (g[5] - g[6]) + (g[8] - g[7]);
-            double mym = (g[2] - g[4]) + (g[5] + g[6]) - (g[7] + g[8]);
-            rho = c.rho_v + C * (c.rho_l - c.rho_v);
-            ux = 3.0 * mxm / rho;
-            uy = 3.0 * mym / rho;
-        }
-        double uu = ux * ux + uy * uy;
-        double w = m.lumped[i];
-        b.Cdiag[i] = C;
-        if (!isfinite(C) || !isfinite(p) || !isfinite(uu)) s[9] += 1.0;
-        s[0] += w * C;
-        s[1] += rho * uu;
-        if (rq.use_band) {
-            double dx = min_image(m.x[i] - rq.cx, rq.period_x), dy = min_image(m.y[i] - rq.cy, rq.period_y);
-            double r = sqrt(dx * dx + dy * dy);
-            if (fabs(r - rq.R) <= rq.band) {
-                s[2] += w;
-                s[3] += w * rho * uu;
-            }
-        }
-        if (C >= 0.95) {
-            s[4] += w;
-            s[5] += w * p;
-        }
-        if (C <= 0.05) {
-            s[6] += w;
-            s[7] += w * p;
-        }
-        mx[0] = fmax(mx[0], uu);
-    }
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m.N; i += gridDim.x * blockDim.x)
+        diag_node<kDev32>(m, c, b, rq, i, s, mx);
     block_reduce_store<10, 1>(s, mx, b.diag_part + (size_t)blockIdx.x * kDiagSlots);
 }
 
@@ -722,30 +755,44 @@ __global__ void __launch_bounds__(kBlock) k_diag_nodes(DevMesh m, Phys c, Bufs b
 __global__ void __launch_bounds__(kBlock) k_diag_edges(DevMesh m, Bufs b, DiagReq rq) {
     double s[1] = {0.0};
     double mx[1] = {-1e300};
-    const int Tp = m.Tp;
-    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < m.E; e += gridDim.x * blockDim.x) {
-        if (m.wall_id[e] != rq.substrate) continue;
-        double Ca = b.Cdiag[m.wall_a[e]], Cb = b.Cdiag[m.wall_b[e]], L = m.wall_len[e];
-        if (Ca >= 0.5 && Cb >= 0.5)
-            s[0] += L;
-        else if (Ca >= 0.5 || Cb >= 0.5) {
-            double hi = fmax(Ca, Cb), lo = fmin(Ca, Cb);
-            s[0] += L * (hi - 0.5) / (hi - lo);
-        }
-    }
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < m.T; t += gridDim.x * blockDim.x) {
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            int ia = m.tri[((k + 1) % 3) * Tp + t], ic = m.tri[((k + 2) % 3) * Tp + t];
-            double Ca = b.Cdiag[ia], Cc = b.Cdiag[ic];
-            if ((Ca >= 0.5) != (Cc >= 0.5)) {
-                double tt = (0.5 - Ca) / (Cc - Ca);
-                double dy = min_image(m.y[ic] - m.y[ia], rq.period_y);
-                mx[0] = fmax(mx[0], m.y[ia] + tt * dy);
-            }
-        }
-    }
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < m.E; e += gridDim.x * blockDim.x)
+        diag_wall(m, b, rq, e, s[0]);
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < m.T; t += gridDim.x * blockDim.x)
+        diag_tri(m, b, rq, t, mx[0]);
     block_reduce_store<1, 1>(s, mx, b.diag_part + (size_t)blockIdx.x * kDiagSlots + 11);
+}
+
+// Tables of the connected components (groups) of the mesh.
+struct GroupTables {
+    const int32_t* node_begin;   // [G] internal node range of each group
+    const int32_t* node_end;
+    const int32_t* tri_begin;    // [G] triangle range
+    const int32_t* tri_end;
+    const int32_t* wall_ptr;     // [G+1] wall edges of each group (CSR)
+    const int32_t* wall_edge;
+    DiagReq* reqs;               // [G] per-group request (written by the host per call)
+    double* out;                 // [G][kDiagSlots]
+    int32_t* cta_groups;         // [G] groups run by k_step_cta32
+};
+
+// One block per group: the same slots as k_diag_nodes/k_diag_edges, reduced
+// over the group's own nodes, wall edges and triangles in a fixed order.
+template <bool kDev32>
+__global__ void __launch_bounds__(kBlock) k_diag_groups(DevMesh m, Phys c, Bufs b, GroupTables gt) {
+    const int g = blockIdx.x;
+    const DiagReq rq = gt.reqs[g];
+    double s[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    double mx[1] = {0.0};
+    for (int i = gt.node_begin[g] + threadIdx.x; i < gt.node_end[g]; i += blockDim.x)
+        diag_node<kDev32>(m, c, b, rq, i, s, mx);
+    __syncthreads();   // the group's C (Cdiag) is complete; it is read below
+    double we[1] = {0.0};
+    double ym[1] = {-1e300};
+    for (int k = gt.wall_ptr[g] + threadIdx.x; k < gt.wall_ptr[g + 1]; k += blockDim.x)
+        diag_wall(m, b, rq, gt.wall_edge[k], we[0]);
+    for (int t = gt.tri_begin[g] + threadIdx.x; t < gt.tri_end[g]; t += blockDim.x) diag_tri(m, b, rq, t, ym[0]);
+    block_reduce_store<10, 1>(s, mx, gt.out + (size_t)g * kDiagSlots);
+    block_reduce_store<1, 1>(we, ym, gt.out + (size_t)g * kDiagSlots + 11);
 }
 
 // One warp per slot: lane l reduces blocks l, l+32, ... in order, then a
@@ -761,6 +808,83 @@ __global__ void k_diag_final(Bufs b) {
     }
     r = is_max ? warp_max(r) : warp_sum(r);
     if (lane == 0) b.diag_out[k] = r;
+}
+
+// ------------------------------------------- one CTA per batch member ------
+// The whole FP32-deviation step of one small batch member in one thread
+// block: the member is a contiguous range of nodes and triangles (its
+// group), every phase is a block-stride loop over that range, and
+// __syncthreads() orders the phases -- no kernel boundary and no grid-wide
+// synchronisation inside the step.  Data written in one phase is read in
+// the next through plain (coherent) loads.
+constexpr int kCtaThreads = 512;
+constexpr int kMaxSweeps = 64;
+struct ChebCoef {
+    float a[kMaxSweeps];
+    float c[kMaxSweeps];
+};
+
+__device__ __forceinline__ void sweep32_node(const DevMesh& m, const Phys& c, const Bufs& b, int i,
+                                             const float* cur, float* prev, float a, float cc, int first,
+                                             bool update) {
+    const int Np = m.Np;
+    float acc[18];
+#pragma unroll
+    for (int q = 0; q < 18; ++q) acc[q] = 0.0f;
+    if (m.ell_w > 0) {
+        for (int k = 0; k < m.ell_w; ++k) {
+            const int j = m.ell_col[k * Np + i];
+            const float v = m.ell_val[k * Np + i];
+#pragma unroll
+            for (int q = 0; q < 18; ++q) acc[q] = fmaf(v, cur[q * Np + j], acc[q]);
+        }
+    } else {
+        for (int k = m.row_ptr[i]; k < m.row_ptr[i + 1]; ++k) {
+            const int j = m.col[k];
+            const float v = m.mval32[k];
+#pragma unroll
+            for (int q = 0; q < 18; ++q) acc[q] = fmaf(v, cur[q * Np + j], acc[q]);
+        }
+    }
+    const float s = cc * m.inv_lumped32[i];
+    float d[18];
+#pragma unroll
+    for (int q = 0; q < 18; ++q) {
+        float xk = cur[q * Np + i];
+        float xm = first ? 0.0f : prev[q * Np + i];
+        float xn = xk + a * (xk - xm) + s * (b.r32[q * Np + i] - acc[q]);
+        if (update)
+            d[q] = xn;
+        else
+            prev[q * Np + i] = xn;
+    }
+    if (update) dev32_update(m, c, b, i, d);
+}
+
+__global__ void __launch_bounds__(kCtaThreads, 1) k_step_cta32(DevMesh m, Phys c, Bufs b, GroupTables gt,
+                                                               const int32_t* __restrict__ groups, ChebCoef cf,
+                                                               int sweeps, float inv_theta) {
+    const int g = groups[blockIdx.x];
+    const int n0 = gt.node_begin[g], n1 = gt.node_end[g], t0 = gt.tri_begin[g], t1 = gt.tri_end[g];
+    const int tid = threadIdx.x, nt = blockDim.x;
+    for (int i = n0 + tid; i < n1; i += nt) mu32_node(m, c, b, i);
+    __syncthreads();
+    for (int t = t0 + tid; t < t1; t += nt) gradmu32_tri(m, b, t);
+    __syncthreads();
+    for (int t = t0 + tid; t < t1; t += nt) element32_tri(m, c, b, t);
+    __syncthreads();
+    for (int i = n0 + tid; i < n1; i += nt) rhs32_node(m, c, b, i, inv_theta);
+    __syncthreads();
+    float* cur = b.e1;
+    float* prv = b.e0;
+    for (int k = 1; k < sweeps; ++k) {
+        const bool last = k == sweeps - 1;
+        for (int i = n0 + tid; i < n1; i += nt) sweep32_node(m, c, b, i, cur, prv, cf.a[k], cf.c[k], k == 1, last);
+        __syncthreads();
+        float* tmp = cur;
+        cur = prv;
+        prv = tmp;
+    }
 }
 
 // --------------------------------------------------------- host side ------
@@ -817,6 +941,16 @@ struct felbm_state {
     cudaEvent_t ev[7] = {};
     bool dev32 = false;   // FELBM_FP32_DEV storage
     bool use_pdl = true;  // programmatic dependent launch between solve sweeps
+    felbm::GroupTables gt{};
+    std::vector<double> gmass0;   // per-group mass at felbm_init
+    // batch schedule (FP32_DEV): groups of at most cta_max_nodes nodes run one
+    // CTA each (k_step_cta32); the rest, a prefix of the node and triangle
+    // ranges, run the tiled kernels.  cta_max_nodes = 0: tiled only.
+    int32_t cta_max_nodes = 0;
+    int32_t n_cta = 0, tiled_N = 0, tiled_T = 0;
+    int32_t* d_cta_groups = nullptr;   // [G] in the workspace
+    cudaStream_t side_stream = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 };
 
 namespace felbm {
@@ -831,7 +965,8 @@ static int ell_width(const HostMesh& h) {
 }
 
 // Layout of the workspace; with base == nullptr only the size is computed.
-static size_t carve(const HostMesh& h, bool dev32, void* base, DevMesh* dm, Bufs* b) {
+static size_t carve(const HostMesh& h, bool dev32, void* base, DevMesh* dm, Bufs* b,
+                    GroupTables* gtab = nullptr) {
     Carver cv(base);
     size_t Np = pad64(h.N), Tp = pad64(h.T);
     size_t nnz = h.row_ptr[h.N], ninc = h.inc_ptr[h.N], nwinc = h.winc_ptr[h.N];
@@ -865,6 +1000,7 @@ static size_t carve(const HostMesh& h, bool dev32, void* base, DevMesh* dm, Bufs
     d.wall_a = cv.take<int32_t>(E);
     d.wall_b = cv.take<int32_t>(E);
     d.wall_id = cv.take<int32_t>(E);
+    d.wall_phi = cv.take<double>(E);
     d.wall_len = cv.take<double>(E);
     d.wall_nx = cv.take<double>(E);
     d.wall_ny = cv.take<double>(E);
@@ -905,6 +1041,18 @@ static size_t carve(const HostMesh& h, bool dev32, void* base, DevMesh* dm, Bufs
     bb.diag_part = cv.take<double>((size_t)kDiagBlocks * kDiagSlots);
     bb.diag_out = cv.take<double>(kDiagSlots);
     bb.Cdiag = cv.take<double>(Np);
+    GroupTables g{};
+    const size_t G = std::max<int32_t>(h.G, 1);
+    g.node_begin = cv.take<int32_t>(G);
+    g.node_end = cv.take<int32_t>(G);
+    g.tri_begin = cv.take<int32_t>(G);
+    g.tri_end = cv.take<int32_t>(G);
+    g.wall_ptr = cv.take<int32_t>(G + 1);
+    g.wall_edge = cv.take<int32_t>(E);
+    g.reqs = cv.take<DiagReq>(G);
+    g.out = cv.take<double>(G * kDiagSlots);
+    g.cta_groups = cv.take<int32_t>(G);
+    if (gtab) *gtab = g;
     if (dm) {
         d.N = h.N;
         d.T = h.T;
@@ -967,9 +1115,8 @@ static void launch_k(bool pdl, void (*kern)(KArgs...), dim3 grid, dim3 block, cu
 // One FP32 Chebyshev sweep: the ELL kernel of the mesh's width, else CSR.
 // pdl: the previous launch on the stream is a sweep (a kernel that waits).
 template <int kFinal>
-static void launch_sweep(felbm_state* st, const Bufs& b, cudaStream_t s, const float* cur, float* prv,
-                         float a, float c, int first, int have_x64, bool pdl) {
-    const DevMesh& m = st->dm;
+static void launch_sweep(felbm_state* st, const DevMesh& m, const Bufs& b, cudaStream_t s, const float* cur,
+                         float* prv, float a, float c, int first, int have_x64, bool pdl) {
     const dim3 block(128);
     const dim3 grid(grid_for(m.N, 128), kFinal == kUpdateDev ? 1 : 2);
     pdl = pdl && st->use_pdl;
@@ -996,8 +1143,8 @@ static void launch_sweep(felbm_state* st, const Bufs& b, cudaStream_t s, const f
 // leave the solution in x1/x0 (FP64 mode, returned) or x64 (mixed mode).
 // bufs: the buffers the solve reads and writes (the state's own, or another
 // set of scratch buffers with the same layout).
-static const double* enqueue_solve(felbm_state* st, const Bufs& b, cudaStream_t s, bool into_psi) {
-    const DevMesh& m = st->dm;
+static const double* enqueue_solve(felbm_state* st, const DevMesh& m, const Bufs& b, cudaStream_t s,
+                                   bool into_psi) {
     const unsigned grid = grid_for(m.N, 128);
     if (st->mode == FELBM_SOLVER_FP64) {
         const double* result = b.x1;
@@ -1021,13 +1168,13 @@ static const double* enqueue_solve(felbm_state* st, const Bufs& b, cudaStream_t 
             const bool last = r == st->rounds - 1 && k == st->sweeps - 1;
             const bool pdl = k > 1;   // the previous launch is a sweep of this round
             if (!last)
-                launch_sweep<kStore>(st, b, s, cur, prv, a, c, k == 1, have_x64, pdl);
+                launch_sweep<kStore>(st, m, b, s, cur, prv, a, c, k == 1, have_x64, pdl);
             else if (!into_psi)
-                launch_sweep<kAddX64>(st, b, s, cur, prv, a, c, k == 1, have_x64, pdl);
+                launch_sweep<kAddX64>(st, m, b, s, cur, prv, a, c, k == 1, have_x64, pdl);
             else if (st->dev32)
-                launch_sweep<kUpdateDev>(st, b, s, cur, prv, a, c, k == 1, have_x64, pdl);
+                launch_sweep<kUpdateDev>(st, m, b, s, cur, prv, a, c, k == 1, have_x64, pdl);
             else
-                launch_sweep<kAddPsi>(st, b, s, cur, prv, a, c, k == 1, have_x64, pdl);
+                launch_sweep<kAddPsi>(st, m, b, s, cur, prv, a, c, k == 1, have_x64, pdl);
             std::swap(cur, prv);
         }
         if (r < st->rounds - 1) {
@@ -1046,6 +1193,8 @@ static int solve_launches(const felbm_state* st) {
 
 static int step_launches(const felbm_state* st) { return (st->dev32 ? 4 : 5) + solve_launches(st); }
 
+int set_schedule(felbm_state* st, int32_t max_nodes);
+
 // Enqueue the kernels of one time step on stream s (optionally with the
 // phase events, recorded as external event nodes of the captured graph).
 static void enqueue_step(felbm_state* st, cudaStream_t s) {
@@ -1056,17 +1205,42 @@ static void enqueue_step(felbm_state* st, cudaStream_t s) {
     };
     mark(0);
     if (st->dev32) {
+        // small batch members: one CTA each, on a side branch of the graph
+        if (st->n_cta > 0) {
+            ChebCoef cf{};
+            for (int k = 1; k < st->sweeps && k < kMaxSweeps; ++k) {
+                cf.a[k] = (float)st->cheb_a[k];
+                cf.c[k] = (float)st->cheb_c[k];
+            }
+            cudaEventRecord(st->ev_fork, s);
+            cudaStreamWaitEvent(st->side_stream, st->ev_fork, 0);
+            k_step_cta32<<<st->n_cta, kCtaThreads, 0, st->side_stream>>>(m, st->phys, b, st->gt, st->gt.cta_groups,
+                                                                         cf, st->sweeps, (float)st->inv_theta);
+            cudaEventRecord(st->ev_join, st->side_stream);
+        }
+        // the rest (a prefix of nodes and triangles): tiled kernels
+        DevMesh mt = m;
+        mt.N = st->tiled_N;
+        mt.T = st->tiled_T;
         // collision is folded into the element, RHS and update kernels
         mark(1);
-        k_mu32<<<grid_for(m.N, kBlock), kBlock, 0, s>>>(m, st->phys, b);
-        mark(2);
-        k_gradmu32<<<grid_for(m.T, kBlock), kBlock, 0, s>>>(m, b);
-        mark(3);
-        k_element32<<<grid_for(m.T, 128), 128, 0, s>>>(m, st->phys, b);
-        mark(4);
-        k_rhs32<<<grid_for(m.N, 128), 128, 0, s>>>(m, st->phys, b, (float)st->inv_theta);
-        mark(5);
-        enqueue_solve(st, st->buf, s, true);
+        if (mt.N > 0) {
+            k_mu32<<<grid_for(mt.N, kBlock), kBlock, 0, s>>>(mt, st->phys, b);
+            mark(2);
+            k_gradmu32<<<grid_for(mt.T, kBlock), kBlock, 0, s>>>(mt, b);
+            mark(3);
+            k_element32<<<grid_for(mt.T, 128), 128, 0, s>>>(mt, st->phys, b);
+            mark(4);
+            k_rhs32<<<grid_for(mt.N, 128), 128, 0, s>>>(mt, st->phys, b, (float)st->inv_theta);
+            mark(5);
+            enqueue_solve(st, mt, st->buf, s, true);
+        } else {
+            mark(2);
+            mark(3);
+            mark(4);
+            mark(5);
+        }
+        if (st->n_cta > 0) cudaStreamWaitEvent(s, st->ev_join, 0);
         mark(6);
         return;
     }
@@ -1083,7 +1257,7 @@ static void enqueue_step(felbm_state* st, cudaStream_t s) {
     else
         k_rhs<true><<<grid_for(m.N, 128), 128, 0, s>>>(m, st->phys, b, st->inv_theta);
     mark(5);
-    enqueue_solve(st, st->buf, s, true);
+    enqueue_solve(st, st->dm, st->buf, s, true);
     mark(6);
 }
 
@@ -1134,7 +1308,7 @@ int felbm_init(const felbm_mesh* mesh, const felbm_params* params, const double*
     st->prm = *params;
     st->stream = static_cast<cudaStream_t>(stream);
     st->dev32 = dev32;
-    carve(h, dev32, d_workspace, &st->dm, &st->buf);
+    carve(h, dev32, d_workspace, &st->dm, &st->buf, &st->gt);
     Phys& ph = st->phys;
     ph.dt = params->dt;
     ph.tau_l = params->tau_l;
@@ -1144,7 +1318,6 @@ int felbm_init(const felbm_mesh* mesh, const felbm_params* params, const double*
     ph.kappa = params->kappa;
     ph.beta = params->beta;
     ph.mobility = params->mobility;
-    for (int k = 0; k < FELBM_MAX_WALL_IDS; ++k) ph.phi_c[k] = params->phi_c[k];
     ph.dt_f = (float)params->dt;
     ph.dt3_f = (float)(params->dt / 3.0);
     ph.dt2h_f = (float)(0.5 * params->dt * params->dt);
@@ -1175,6 +1348,8 @@ int felbm_init(const felbm_mesh* mesh, const felbm_params* params, const double*
     const double scale = params->lap_mode == FELBM_LAP_PAPER ? 1.0 : 2.0 / 3.0;
     std::vector<double> inv_vol(h.N), inv_lumped(h.N), lval(h.row_ptr[h.N]);
     std::vector<float> inv_lumped32(h.N), mval32(h.mass.begin(), h.mass.end());
+    std::vector<double> wall_phi(h.E);
+    for (int32_t e = 0; e < h.E; ++e) wall_phi[e] = params->phi_c[h.wall_id[e]];
     const int ellw = st->dm.ell_w;
     std::vector<int32_t> ell_col((size_t)std::max(ellw, 1) * st->dm.Np, 0);
     std::vector<float> ell_val((size_t)std::max(ellw, 1) * st->dm.Np, 0.0f);
@@ -1247,6 +1422,7 @@ int felbm_init(const felbm_mesh* mesh, const felbm_params* params, const double*
     UP(d.wall_a, h.wall_a);
     UP(d.wall_b, h.wall_b);
     UP(d.wall_id, h.wall_id);
+    UP(d.wall_phi, wall_phi);
     UP(d.wall_len, h.wall_len);
     UP(d.wall_nx, h.wall_nx);
     UP(d.wall_ny, h.wall_ny);
@@ -1256,6 +1432,12 @@ int felbm_init(const felbm_mesh* mesh, const felbm_params* params, const double*
     UP(d.y, h.y);
     UP(d.perm, h.perm);
     UP(d.iperm, h.iperm);
+    UP(st->gt.node_begin, h.grp_node_begin);
+    UP(st->gt.node_end, h.grp_node_end);
+    UP(st->gt.tri_begin, h.grp_tri_begin);
+    UP(st->gt.tri_end, h.grp_tri_end);
+    UP(st->gt.wall_ptr, h.grp_wall_ptr);
+    UP(st->gt.wall_edge, h.grp_wall_edge);
 #undef UP
     if (e != cudaSuccess) return fail(e, "felbm_init: upload");
     e = cudaMemcpyAsync(st->buf.stage, C0, sizeof(double) * h.N, cudaMemcpyHostToDevice, s);
@@ -1280,8 +1462,69 @@ int felbm_init(const felbm_mesh* mesh, const felbm_params* params, const double*
         return rc;
     }
     st->mass0 = dg.mass;
+    std::vector<felbm_diag> gd(std::max<int32_t>(h.G, 1));
+    rc = felbm_diagnostics_groups(st, nullptr, h.G, gd.data());
+    if (rc != FELBM_OK && rc != FELBM_ERR_NONFINITE) {
+        *out = nullptr;
+        delete st;
+        return rc;
+    }
+    st->gmass0.resize(h.G);
+    for (int32_t g = 0; g < h.G; ++g) st->gmass0[g] = gd[g].mass;
+    rc = set_schedule(st, 0);
+    if (rc != FELBM_OK) {
+        *out = nullptr;
+        delete st;
+        return rc;
+    }
     return FELBM_OK;
 }
+
+}  // extern "C"
+
+namespace felbm {
+
+// Split the groups: those of at most max_nodes nodes run one CTA each.  The
+// groups are laid out largest first, so the others form a prefix.
+int set_schedule(felbm_state* st, int32_t max_nodes) {
+    const HostMesh& h = st->hm;
+    std::vector<int32_t> cta;
+    int32_t tiled_N = 0, tiled_T = 0;
+    for (int32_t g = 0; g < h.G; ++g) {
+        if (st->dev32 && max_nodes > 0 && h.grp_size[g] <= max_nodes) {
+            cta.push_back(g);
+        } else {
+            tiled_N = std::max(tiled_N, h.grp_node_end[g]);
+            tiled_T = std::max(tiled_T, h.grp_tri_end[g]);
+        }
+    }
+    for (int32_t g : cta)
+        if (h.grp_node_begin[g] < tiled_N || h.grp_tri_begin[g] < tiled_T) {
+            set_error("felbm: batch schedule needs the small members after the large ones");
+            return FELBM_ERR_INVALID_ARG;
+        }
+    if (st->sweeps >= kMaxSweeps && !cta.empty()) {
+        set_error("felbm: too many solver sweeps for the per-member CTA schedule");
+        return FELBM_ERR_UNSUPPORTED;
+    }
+    if (!cta.empty()) {
+        if (!st->side_stream) FELBM_CUDA(cudaStreamCreateWithFlags(&st->side_stream, cudaStreamNonBlocking));
+        if (!st->ev_fork) FELBM_CUDA(cudaEventCreateWithFlags(&st->ev_fork, cudaEventDisableTiming));
+        if (!st->ev_join) FELBM_CUDA(cudaEventCreateWithFlags(&st->ev_join, cudaEventDisableTiming));
+        FELBM_CUDA(cudaMemcpyAsync(st->gt.cta_groups, cta.data(), sizeof(int32_t) * cta.size(),
+                                   cudaMemcpyHostToDevice, st->stream));
+        FELBM_CUDA(cudaStreamSynchronize(st->stream));
+    }
+    st->cta_max_nodes = cta.empty() ? 0 : max_nodes;
+    st->n_cta = (int32_t)cta.size();
+    st->tiled_N = tiled_N;
+    st->tiled_T = tiled_T;
+    return FELBM_OK;
+}
+
+}  // namespace felbm
+
+extern "C" {
 
 static int build_graph(felbm_state* st) {
     if (!st->cap_stream) FELBM_CUDA(cudaStreamCreateWithFlags(&st->cap_stream, cudaStreamNonBlocking));
@@ -1349,11 +1592,11 @@ int felbm_timing_get(felbm_state* st, felbm_step_timing* out) {
     return FELBM_OK;
 }
 
-int felbm_diagnostics(felbm_state* st, const felbm_diag_request* req, felbm_diag* out) {
-    if (!st || !out) {
-        set_error("felbm_diagnostics: invalid argument");
-        return FELBM_ERR_INVALID_ARG;
-    }
+}  // extern "C"
+
+namespace felbm {
+
+static DiagReq make_req(const felbm_state* st, const felbm_diag_request* req) {
     DiagReq rq{};
     rq.period_x = st->hm.period[0];
     rq.period_y = st->hm.period[1];
@@ -1365,6 +1608,63 @@ int felbm_diagnostics(felbm_state* st, const felbm_diag_request* req, felbm_diag
         rq.R = req->radius;
         rq.band = req->band;
     }
+    return rq;
+}
+
+// felbm_diag from the reduced slots; the contact angle uses the mean height
+// of the substrate wall nodes among the given wall edges.
+static felbm_diag fill_diag(const felbm_state* st, const double* v, double mass0, int64_t nodes, int substrate,
+                            const int32_t* edges, int32_t n_edges) {
+    const HostMesh& h = st->hm;
+    felbm_diag d{};
+    d.step = st->step;
+    d.mass = v[0];
+    d.mass0 = mass0;
+    d.mass_drift_rel = mass0 != 0.0 ? (v[0] - mass0) / mass0 : 0.0;
+    d.kinetic_energy = 0.5 * v[1] / (double)std::max<int64_t>(nodes, 1);
+    d.max_u = std::sqrt(v[10]);
+    d.interface_rho_uu = v[2] > 0.0 ? v[3] / v[2] : 0.0;
+    d.p_in = v[5] / std::max(v[4], 1e-300);
+    d.p_out = v[7] / std::max(v[6], 1e-300);
+    d.delta_p = d.p_in - d.p_out;
+    d.wetted_length = v[11];
+    double ysum = 0.0;
+    int ny = 0;
+    std::vector<int32_t> nodes_seen;
+    for (int32_t k = 0; k < n_edges; ++k) {
+        int32_t e = edges ? edges[k] : k;
+        if (h.wall_id[e] != substrate) continue;
+        nodes_seen.push_back(h.wall_a[e]);
+        nodes_seen.push_back(h.wall_b[e]);
+    }
+    std::sort(nodes_seen.begin(), nodes_seen.end());
+    nodes_seen.erase(std::unique(nodes_seen.begin(), nodes_seen.end()), nodes_seen.end());
+    for (int32_t n : nodes_seen) {
+        ysum += h.y[n];
+        ++ny;
+    }
+    d.height = ny ? v[12] - ysum / ny : std::nan("");
+    double b = d.wetted_length, hh = d.height;
+    if (ny && hh > 0.0 && b > 0.0) {
+        double r = (4.0 * hh * hh + b * b) / (8.0 * hh);
+        d.theta_deg = std::atan2(b, 2.0 * (r - hh)) * 180.0 / M_PI;
+    } else {
+        d.theta_deg = std::nan("");
+    }
+    d.status = v[9] > 0.0 ? FELBM_ERR_NONFINITE : FELBM_OK;
+    return d;
+}
+
+}  // namespace felbm
+
+extern "C" {
+
+int felbm_diagnostics(felbm_state* st, const felbm_diag_request* req, felbm_diag* out) {
+    if (!st || !out) {
+        set_error("felbm_diagnostics: invalid argument");
+        return FELBM_ERR_INVALID_ARG;
+    }
+    DiagReq rq = make_req(st, req);
     cudaStream_t s = st->stream;
     if (st->dev32)
         k_diag_nodes<true><<<kDiagBlocks, kBlock, 0, s>>>(st->dm, st->phys, st->buf, rq);
@@ -1376,44 +1676,46 @@ int felbm_diagnostics(felbm_state* st, const felbm_diag_request* req, felbm_diag
     double v[kDiagSlots];
     FELBM_CUDA(cudaMemcpyAsync(v, st->buf.diag_out, sizeof v, cudaMemcpyDeviceToHost, s));
     FELBM_CUDA(cudaStreamSynchronize(s));
-    const HostMesh& h = st->hm;
-    felbm_diag d{};
-    d.step = st->step;
-    d.mass = v[0];
-    d.mass0 = st->mass0;
-    d.mass_drift_rel = st->mass0 != 0.0 ? (v[0] - st->mass0) / st->mass0 : 0.0;
-    d.kinetic_energy = 0.5 * v[1] / h.N;
-    d.max_u = std::sqrt(v[10]);
-    d.interface_rho_uu = v[2] > 0.0 ? v[3] / v[2] : 0.0;
-    d.p_in = v[5] / std::max(v[4], 1e-300);
-    d.p_out = v[7] / std::max(v[6], 1e-300);
-    d.delta_p = d.p_in - d.p_out;
-    d.wetted_length = v[11];
-    // mean height of the substrate wall nodes
-    double ysum = 0.0;
-    int ny = 0;
-    std::vector<char> seen(h.N, 0);
-    for (int32_t e = 0; e < h.E; ++e) {
-        if (h.wall_id[e] != rq.substrate) continue;
-        for (int32_t n : {h.wall_a[e], h.wall_b[e]})
-            if (!seen[n]) {
-                seen[n] = 1;
-                ysum += h.y[n];
-                ++ny;
-            }
-    }
-    d.height = ny ? v[12] - ysum / ny : std::nan("");
-    double b = d.wetted_length, hh = d.height;
-    if (ny && hh > 0.0 && b > 0.0) {
-        double r = (4.0 * hh * hh + b * b) / (8.0 * hh);
-        d.theta_deg = std::atan2(b, 2.0 * (r - hh)) * 180.0 / M_PI;
-    } else {
-        d.theta_deg = std::nan("");
-    }
-    d.status = v[9] > 0.0 ? FELBM_ERR_NONFINITE : FELBM_OK;
-    *out = d;
-    if (d.status != FELBM_OK) {
+    *out = fill_diag(st, v, st->mass0, st->hm.N, rq.substrate, nullptr, st->hm.E);
+    if (out->status != FELBM_OK) {
         set_error("felbm_diagnostics: non-finite values in the state");
+        return FELBM_ERR_NONFINITE;
+    }
+    return FELBM_OK;
+}
+
+int felbm_diagnostics_groups(felbm_state* st, const felbm_diag_request* reqs, int32_t n_groups, felbm_diag* out) {
+    if (!st || !out || n_groups != st->hm.G || n_groups < 1) {
+        set_error("felbm_diagnostics_groups: invalid argument (n_groups must equal the mesh's group count)");
+        return FELBM_ERR_INVALID_ARG;
+    }
+    const HostMesh& h = st->hm;
+    std::vector<DiagReq> rq(n_groups);
+    for (int32_t g = 0; g < n_groups; ++g) {
+        rq[g] = make_req(st, reqs ? reqs + g : nullptr);
+        rq[g].period_x = h.grp_period_x[g];
+        rq[g].period_y = h.grp_period_y[g];
+    }
+    cudaStream_t s = st->stream;
+    FELBM_CUDA(cudaMemcpyAsync(st->gt.reqs, rq.data(), sizeof(DiagReq) * n_groups, cudaMemcpyHostToDevice, s));
+    if (st->dev32)
+        k_diag_groups<true><<<n_groups, kBlock, 0, s>>>(st->dm, st->phys, st->buf, st->gt);
+    else
+        k_diag_groups<false><<<n_groups, kBlock, 0, s>>>(st->dm, st->phys, st->buf, st->gt);
+    FELBM_CUDA(cudaGetLastError());
+    std::vector<double> v((size_t)n_groups * kDiagSlots);
+    FELBM_CUDA(cudaMemcpyAsync(v.data(), st->gt.out, sizeof(double) * v.size(), cudaMemcpyDeviceToHost, s));
+    FELBM_CUDA(cudaStreamSynchronize(s));
+    bool bad = false;
+    for (int32_t g = 0; g < n_groups; ++g) {
+        const double* vg = v.data() + (size_t)g * kDiagSlots;
+        double m0 = g < (int32_t)st->gmass0.size() ? st->gmass0[g] : vg[0];
+        out[g] = fill_diag(st, vg, m0, h.grp_size[g], rq[g].substrate, h.grp_wall_edge.data() + h.grp_wall_ptr[g],
+                           h.grp_wall_ptr[g + 1] - h.grp_wall_ptr[g]);
+        bad = bad || out[g].status != FELBM_OK;
+    }
+    if (bad) {
+        set_error("felbm_diagnostics_groups: non-finite values in the state");
         return FELBM_ERR_NONFINITE;
     }
     return FELBM_OK;
@@ -1508,7 +1810,7 @@ int felbm_mass_solve(felbm_state* st, const double* B, double* X, int32_t k) {
         k_cheb_start<false><<<grid_for(m.N, kBlock), kBlock, 0, s>>>(m, b, st->inv_theta);
     else
         k_cheb_start<true><<<grid_for(m.N, kBlock), kBlock, 0, s>>>(m, b, st->inv_theta);
-    const double* result = enqueue_solve(st, b, s, false);
+    const double* result = enqueue_solve(st, st->dm, b, s, false);
     k_gather_out<<<grid_for(m.N, kBlock), kBlock, 0, s>>>(m, result, b.stage, k);
     FELBM_CUDA(cudaGetLastError());
     FELBM_CUDA(cudaMemcpyAsync(X, b.stage, sizeof(double) * k * m.N, cudaMemcpyDeviceToHost, s));
@@ -1596,16 +1898,120 @@ int felbm_mass_solve_static(felbm_state* st, const double* d_B, double* d_X, int
         k_cheb_start<false><<<grid_for(m.N, kBlock), kBlock, 0, s>>>(m, sb, st->inv_theta);
     else
         k_cheb_start<true><<<grid_for(m.N, kBlock), kBlock, 0, s>>>(m, sb, st->inv_theta);
-    const double* result = enqueue_solve(st, sb, s, false);
+    const double* result = enqueue_solve(st, st->dm, sb, s, false);
     k_gather_out<<<grid_for(m.N, kBlock), kBlock, 0, s>>>(m, result, d_X, k);
     FELBM_CUDA(cudaGetLastError());
     return FELBM_OK;
+}
+
+int felbm_batch_schedule(felbm_state* st, int32_t cta_max_nodes) {
+    if (!st || cta_max_nodes < 0) {
+        set_error("felbm_batch_schedule: invalid argument");
+        return FELBM_ERR_INVALID_ARG;
+    }
+    FELBM_CUDA(cudaStreamSynchronize(st->stream));
+    int rc = set_schedule(st, cta_max_nodes);
+    if (rc) return rc;
+    drop_graph(st);
+    return FELBM_OK;
+}
+
+}  // extern "C"
+
+namespace felbm {
+
+// Copy the FP32-deviation state (dpsi, C, p, u) to or from the staging buffer.
+static int save_restore_dev32(felbm_state* st, bool save) {
+    const DevMesh& m = st->dm;
+    const Bufs& b = st->buf;
+    char* stage = reinterpret_cast<char*>(b.stage);
+    const size_t nf = 18 * (size_t)m.Np * sizeof(float), nd = (size_t)m.Np * sizeof(double),
+                 n1 = (size_t)m.Np * sizeof(float);
+    void* dev[5] = {b.dpsi, b.C, b.p32, b.ux32, b.uy32};
+    size_t len[5] = {nf, nd, n1, n1, n1};
+    size_t off = 0;
+    for (int k = 0; k < 5; ++k) {
+        void* dst = save ? (void*)(stage + off) : dev[k];
+        const void* src = save ? dev[k] : (const void*)(stage + off);
+        FELBM_CUDA(cudaMemcpyAsync(dst, src, len[k], cudaMemcpyDeviceToDevice, st->stream));
+        off += (len[k] + 255) & ~size_t(255);
+    }
+    return FELBM_OK;
+}
+
+}  // namespace felbm
+
+extern "C" {
+
+int felbm_autotune(felbm_state* st, int32_t trials, felbm_tune_result* out) {
+    if (!st || !out || trials < 1) {
+        set_error("felbm_autotune: invalid argument");
+        return FELBM_ERR_INVALID_ARG;
+    }
+    *out = felbm_tune_result{};
+    const HostMesh& h = st->hm;
+    if (!st->dev32 || h.G < 2) {
+        out->cta_max_nodes = 0;
+        out->n_candidates = 0;
+        return felbm_batch_schedule(st, 0);
+    }
+    FELBM_CUDA(cudaStreamSynchronize(st->stream));
+    int rc = save_restore_dev32(st, true);
+    if (rc) return rc;
+    const int64_t step0 = st->step;
+    const bool timing0 = st->timing;
+    st->timing = false;
+    cudaEvent_t e0, e1;
+    FELBM_CUDA(cudaEventCreate(&e0));
+    FELBM_CUDA(cudaEventCreate(&e1));
+    std::vector<int32_t> cand = {0, 1 << 11, 1 << 12, 1 << 13, 1 << 14, 1 << 15, 1 << 16, 1 << 17};
+    int last_n_cta = -1;
+    float best = 1e30f;
+    int32_t best_t = 0;
+    for (int32_t t : cand) {
+        int32_t n_cta = 0;
+        for (int32_t g = 0; g < h.G; ++g) n_cta += (t > 0 && h.grp_size[g] <= t);
+        if (n_cta == last_n_cta) continue;   // same split as the previous candidate
+        last_n_cta = n_cta;
+        if ((rc = felbm_batch_schedule(st, t)) != FELBM_OK) break;
+        if ((rc = felbm_step(st, 1)) != FELBM_OK) break;
+        FELBM_CUDA(cudaEventRecord(e0, st->stream));
+        if ((rc = felbm_step(st, trials)) != FELBM_OK) break;
+        FELBM_CUDA(cudaEventRecord(e1, st->stream));
+        FELBM_CUDA(cudaEventSynchronize(e1));
+        float ms = 0.0f;
+        FELBM_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        ms /= trials;
+        if (out->n_candidates < 16) {
+            out->candidates[out->n_candidates] = t;
+            out->step_ms[out->n_candidates] = ms;
+            out->n_candidates++;
+        }
+        if (ms < best) {
+            best = ms;
+            best_t = t;
+        }
+        if ((rc = save_restore_dev32(st, false)) != FELBM_OK) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    int rc2 = save_restore_dev32(st, false);
+    FELBM_CUDA(cudaStreamSynchronize(st->stream));
+    st->step = step0;
+    st->timing = timing0;
+    if (rc) return rc;
+    if (rc2) return rc2;
+    out->cta_max_nodes = best_t;
+    return felbm_batch_schedule(st, best_t);
 }
 
 void felbm_state_destroy(felbm_state* st) {
     if (!st) return;
     drop_graph(st);
     if (st->cap_stream) cudaStreamDestroy(st->cap_stream);
+    if (st->side_stream) cudaStreamDestroy(st->side_stream);
+    if (st->ev_fork) cudaEventDestroy(st->ev_fork);
+    if (st->ev_join) cudaEventDestroy(st->ev_join);
     for (auto& e : st->ev)
         if (e) cudaEventDestroy(e);
     delete st;

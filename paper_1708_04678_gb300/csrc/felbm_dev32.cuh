@@ -37,9 +37,7 @@ __device__ __forceinline__ float gamma32(float ux, float uy, float uu15) {
 
 // ------------------------------------------------- chemical potential ------
 // Same arithmetic as k_mu (FP64), FP32 output.
-__global__ void __launch_bounds__(kBlock) k_mu32(DevMesh m, Phys c, Bufs b) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= m.N) return;
+__device__ __forceinline__ void mu32_node(const DevMesh& m, const Phys& c, const Bufs& b, int i) {
     double Ci = b.C[i];
     double lap = 0.0;
     for (int k = m.row_ptr[i]; k < m.row_ptr[i + 1]; ++k) lap += m.lval[k] * (b.C[m.col[k]] - Ci);
@@ -48,14 +46,17 @@ __global__ void __launch_bounds__(kBlock) k_mu32(DevMesh m, Phys c, Bufs b) {
         int e = m.winc_edge[k];
         double Ca = b.C[m.wall_a[e]], Cb = b.C[m.wall_b[e]];
         double s = 0.5 * (Ca + Cb) - (Ca * Ca + Ca * Cb + Cb * Cb) * (1.0 / 3.0);
-        wall -= c.phi_c[m.wall_id[e]] * m.wall_len[e] * s;
+        wall -= m.wall_phi[e] * m.wall_len[e] * s;
     }
     b.mu32[i] = (float)(2.0 * c.beta * Ci * (Ci - 1.0) * (2.0 * Ci - 1.0) - (c.kappa * lap + wall * m.inv_vol[i]));
 }
 
-__global__ void __launch_bounds__(kBlock) k_gradmu32(DevMesh m, Bufs b) {
-    int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= m.T) return;
+__global__ void __launch_bounds__(kBlock) k_mu32(DevMesh m, Phys c, Bufs b) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < m.N) mu32_node(m, c, b, i);
+}
+
+__device__ __forceinline__ void gradmu32_tri(const DevMesh& m, const Bufs& b, int t) {
     const int Tp = m.Tp;
     int v0 = m.tri[t], v1 = m.tri[Tp + t], v2 = m.tri[2 * Tp + t];
     float m0 = b.mu32[v0], d1 = b.mu32[v1] - m0, d2 = b.mu32[v2] - m0;
@@ -63,12 +64,15 @@ __global__ void __launch_bounds__(kBlock) k_gradmu32(DevMesh m, Bufs b) {
     b.gmu32[Tp + t] = d1 * m.grad32[3 * Tp + t] + d2 * m.grad32[5 * Tp + t];
 }
 
+__global__ void __launch_bounds__(kBlock) k_gradmu32(DevMesh m, Bufs b) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < m.T) gradmu32_tri(m, b, t);
+}
+
 // ------------------------------- forces and element residual (FP32) ------
 // R_a = A (Phi_a - e_a . grad psi_hat_a), psi_hat = psi^eq + (1 - omega) dpsi,
 // gradients formed from differences to vertex 0 (sum of the b_v is zero).
-__global__ void __launch_bounds__(128) k_element32(DevMesh m, Phys c, Bufs b) {
-    int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= m.T) return;
+__device__ __forceinline__ void element32_tri(const DevMesh& m, const Phys& c, const Bufs& b, int t) {
     const int Tp = m.Tp, Np = m.Np;
     int v[3];
     float bx[3], by[3];
@@ -161,13 +165,16 @@ __global__ void __launch_bounds__(128) k_element32(DevMesh m, Phys c, Bufs b) {
     for (int k = 0; k < 9; ++k) dst[k] = make_float2(out[2 * k], out[2 * k + 1]);
 }
 
+__global__ void __launch_bounds__(128) k_element32(DevMesh m, Phys c, Bufs b) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < m.T) element32_tri(m, c, b, t);
+}
+
 // ------------------------------------------ streaming RHS gather (FP32) ----
 // As k_rhs; the wall term needs psi_hat_opp - psi_hat at a node, which in the
 // split form is  g: -2 w rho (e.u) + (1-omega)(dg_opp - dg),
 //                h: -6 w C (e.u)   + (1-omega)(dh_opp - dh).
-__global__ void __launch_bounds__(128) k_rhs32(DevMesh m, Phys c, Bufs b, float inv_theta) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= m.N) return;
+__device__ __forceinline__ void rhs32_node(const DevMesh& m, const Phys& c, const Bufs& b, int i, float inv_theta) {
     const int Np = m.Np;
     float acc[18];
 #pragma unroll
@@ -230,6 +237,11 @@ __global__ void __launch_bounds__(128) k_rhs32(DevMesh m, Phys c, Bufs b, float 
         b.r32[q * Np + i] = acc[q];
         b.e1[q * Np + i] = acc[q] * s;
     }
+}
+
+__global__ void __launch_bounds__(128) k_rhs32(DevMesh m, Phys c, Bufs b, float inv_theta) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < m.N) rhs32_node(m, c, b, i, inv_theta);
 }
 
 // ---------------------------- update of fields and deviations (node) ------

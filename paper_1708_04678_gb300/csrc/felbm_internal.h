@@ -39,6 +39,13 @@ struct HostMesh {
     std::vector<int32_t> winc_ptr, winc_edge;
     double min_area = 0.0, total_area = 0.0;
     int32_t max_degree = 0, bandwidth = 0;
+    // connected components ("groups"), numbered by their lowest caller node
+    // id; each occupies a contiguous range of internal nodes and triangles
+    int32_t G = 0;
+    std::vector<int32_t> grp_node_begin, grp_node_end, grp_tri_begin, grp_tri_end;
+    std::vector<int32_t> grp_wall_ptr, grp_wall_edge;   // wall edges of each group (CSR)
+    std::vector<int32_t> grp_first_caller, grp_size;
+    std::vector<double> grp_period_x, grp_period_y;      // periodic lengths of each group
 };
 
 }  // namespace felbm

@@ -8,6 +8,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <climits>
 #include <cstring>
 #include <deque>
 #include <numeric>
@@ -100,15 +101,15 @@ static std::vector<int32_t> rcm_order(int32_t N, const std::vector<int32_t>& adj
     return order;
 }
 
+// node_px / node_py: periodic lengths of the sub-mesh each node belongs to
+// (one value for a single mesh; per member mesh for a batch).
 static int build_mesh(const double* xy, int32_t N, const int32_t* tri_in, int32_t T,
-                      const int32_t* wall_edges, const int32_t* wall_id, int32_t E, double px,
-                      double py, HostMesh& m) {
+                      const int32_t* wall_edges, const int32_t* wall_id, int32_t E,
+                      const std::vector<double>& node_px, const std::vector<double>& node_py, HostMesh& m) {
     char buf[256];
     m.N = N;
     m.T = T;
     m.E = E;
-    m.period[0] = px;
-    m.period[1] = py;
     for (int64_t i = 0; i < 3LL * T; ++i)
         if (tri_in[i] < 0 || tri_in[i] >= N) {
             set_error("felbm_mesh_create: triangle node id out of range");
@@ -139,7 +140,12 @@ static int build_mesh(const double* xy, int32_t N, const int32_t* tri_in, int32_
         const int32_t* v = tri_in + 3 * (size_t)t;
         lx[3 * t] = 0.0;
         ly[3 * t] = 0.0;
+        const double px = node_px[v[0]], py = node_py[v[0]];
         for (int k = 1; k < 3; ++k) {
+            if (node_px[v[k]] != px || node_py[v[k]] != py) {
+                set_error("felbm_mesh_create_batch: triangle joins two member meshes");
+                return FELBM_ERR_BAD_MESH;
+            }
             lx[3 * t + k] = min_image(xy[2 * v[k]] - xy[2 * v[0]], px);
             ly[3 * t + k] = min_image(xy[2 * v[k] + 1] - xy[2 * v[0] + 1], py);
         }
@@ -243,6 +249,34 @@ static int build_mesh(const double* xy, int32_t N, const int32_t* tri_in, int32_
         }
     }
     m.perm = rcm_order(N, adj_ptr, adj);
+    // Several components (a batch): reverse Cuthill-McKee emits each one as a
+    // run; order the runs by size, largest first, keeping each run's order,
+    // so that the large members form a prefix of the node and triangle
+    // ranges (the tiled kernels of a hybrid batch schedule cover the prefix).
+    {
+        std::vector<int32_t> comp_of(N, -1), csize;
+        for (int32_t s0 = 0; s0 < N; ++s0) {
+            if (comp_of[s0] >= 0) continue;
+            int32_t id = (int32_t)csize.size();
+            csize.push_back(0);
+            std::deque<int32_t> q{s0};
+            comp_of[s0] = id;
+            while (!q.empty()) {
+                int32_t v = q.front();
+                q.pop_front();
+                csize[id]++;
+                for (int32_t k = adj_ptr[v]; k < adj_ptr[v + 1]; ++k)
+                    if (comp_of[adj[k]] < 0) {
+                        comp_of[adj[k]] = id;
+                        q.push_back(adj[k]);
+                    }
+            }
+        }
+        if (csize.size() > 1)
+            std::stable_sort(m.perm.begin(), m.perm.end(), [&](int32_t a, int32_t b) {
+                return csize[comp_of[a]] > csize[comp_of[b]];
+            });
+    }
     m.iperm.assign(N, 0);
     for (int32_t n = 0; n < N; ++n) m.iperm[m.perm[n]] = n;
 
@@ -386,6 +420,83 @@ static int build_mesh(const double* xy, int32_t N, const int32_t* tri_in, int32_
             m.winc_edge[fill[m.wall_b[e]]++] = e;
         }
     }
+
+    // ---- connected components (groups) -----------------------------------
+    // Reverse Cuthill-McKee emits each component as one run of internal ids,
+    // and triangles are sorted by their lowest node, so a group is a node
+    // range and a triangle range.
+    std::vector<int32_t> comp(N, -1);
+    std::vector<int32_t> runs;   // first internal node of each run
+    for (int32_t n = 0; n < N; ++n) {
+        if (comp[n] >= 0) continue;
+        int32_t id = (int32_t)runs.size();
+        runs.push_back(n);
+        std::deque<int32_t> q{n};
+        comp[n] = id;
+        while (!q.empty()) {
+            int32_t v = q.front();
+            q.pop_front();
+            for (int32_t k = m.row_ptr[v]; k < m.row_ptr[v + 1]; ++k) {
+                int32_t w = m.col[k];
+                if (comp[w] < 0) {
+                    comp[w] = id;
+                    q.push_back(w);
+                }
+            }
+        }
+    }
+    const int32_t G = (int32_t)runs.size();
+    std::vector<int32_t> cbeg(G, N), cend(G, 0), cmin(G, INT32_MAX), ccount(G, 0);
+    for (int32_t n = 0; n < N; ++n) {
+        int32_t c = comp[n];
+        cbeg[c] = std::min(cbeg[c], n);
+        cend[c] = std::max(cend[c], n + 1);
+        cmin[c] = std::min(cmin[c], m.perm[n]);
+        ccount[c]++;
+    }
+    for (int32_t c = 0; c < G; ++c)
+        if (cend[c] - cbeg[c] != ccount[c]) {
+            set_error("felbm_mesh_create: internal error, component not contiguous");
+            return FELBM_ERR_BAD_MESH;
+        }
+    std::vector<int32_t> order(G);
+    std::iota(order.begin(), order.end(), 0);
+    std::sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return cmin[a] < cmin[b]; });
+    std::vector<int32_t> gid(G);
+    for (int32_t g = 0; g < G; ++g) gid[order[g]] = g;
+    m.G = G;
+    m.grp_node_begin.assign(G, 0);
+    m.grp_node_end.assign(G, 0);
+    m.grp_tri_begin.assign(G, T);
+    m.grp_tri_end.assign(G, 0);
+    m.grp_first_caller.assign(G, 0);
+    m.grp_size.assign(G, 0);
+    m.grp_period_x.assign(G, 0.0);
+    m.grp_period_y.assign(G, 0.0);
+    for (int32_t c = 0; c < G; ++c) {
+        int32_t g = gid[c];
+        m.grp_node_begin[g] = cbeg[c];
+        m.grp_node_end[g] = cend[c];
+        m.grp_first_caller[g] = cmin[c];
+        m.grp_size[g] = cend[c] - cbeg[c];
+        m.grp_period_x[g] = node_px[cmin[c]];
+        m.grp_period_y[g] = node_py[cmin[c]];
+    }
+    for (int32_t t = 0; t < T; ++t) {
+        int32_t g = gid[comp[m.tri[t]]];
+        m.grp_tri_begin[g] = std::min(m.grp_tri_begin[g], t);
+        m.grp_tri_end[g] = std::max(m.grp_tri_end[g], t + 1);
+    }
+    for (int32_t g = 0; g < G; ++g)
+        if (m.grp_tri_begin[g] > m.grp_tri_end[g]) m.grp_tri_begin[g] = m.grp_tri_end[g] = 0;
+    m.grp_wall_ptr.assign(G + 1, 0);
+    for (int32_t e = 0; e < E; ++e) m.grp_wall_ptr[gid[comp[m.wall_a[e]]] + 1]++;
+    for (int32_t g = 0; g < G; ++g) m.grp_wall_ptr[g + 1] += m.grp_wall_ptr[g];
+    m.grp_wall_edge.assign(E, 0);
+    {
+        std::vector<int32_t> fill(m.grp_wall_ptr.begin(), m.grp_wall_ptr.end() - 1);
+        for (int32_t e = 0; e < E; ++e) m.grp_wall_edge[fill[gid[comp[m.wall_a[e]]]]++] = e;
+    }
     return FELBM_OK;
 }
 
@@ -428,10 +539,82 @@ int felbm_mesh_create(const double* xy, int32_t n_nodes, const int32_t* tri, int
     }
     int rc;
     try {
-        rc = felbm::build_mesh(xy, n_nodes, tri, n_tri, wall_edges, wall_id, n_wall_edges, period_x,
-                               period_y, m->h);
+        std::vector<double> npx(n_nodes, period_x), npy(n_nodes, period_y);
+        m->h.period[0] = period_x;
+        m->h.period[1] = period_y;
+        rc = felbm::build_mesh(xy, n_nodes, tri, n_tri, wall_edges, wall_id, n_wall_edges, npx, npy, m->h);
     } catch (const std::exception& ex) {
         felbm::set_error(std::string("felbm_mesh_create: ") + ex.what());
+        rc = FELBM_ERR_INVALID_ARG;
+    }
+    if (rc != FELBM_OK) {
+        delete m;
+        return rc;
+    }
+    *out = m;
+    return FELBM_OK;
+}
+
+int felbm_mesh_create_batch(int32_t n_meshes, const felbm_mesh_desc* meshes, felbm_mesh** out) {
+    if (!out || !meshes || n_meshes < 1) {
+        felbm::set_error("felbm_mesh_create_batch: invalid argument");
+        return FELBM_ERR_INVALID_ARG;
+    }
+    *out = nullptr;
+    int64_t N = 0, T = 0, E = 0;
+    for (int32_t k = 0; k < n_meshes; ++k) {
+        const felbm_mesh_desc& d = meshes[k];
+        if (!d.xy || !d.tri || d.n_nodes <= 0 || d.n_tri <= 0 || d.n_wall_edges < 0 ||
+            (d.n_wall_edges > 0 && (!d.wall_edges || !d.wall_id)) || d.period_x < 0.0 || d.period_y < 0.0) {
+            felbm::set_error("felbm_mesh_create_batch: invalid member mesh");
+            return FELBM_ERR_INVALID_ARG;
+        }
+        N += d.n_nodes;
+        T += d.n_tri;
+        E += d.n_wall_edges;
+    }
+    if (N > INT32_MAX || 3 * T > INT32_MAX) {
+        felbm::set_error("felbm_mesh_create_batch: batch too large for 32-bit indices");
+        return FELBM_ERR_INVALID_ARG;
+    }
+    std::vector<double> xy(2 * N), npx(N), npy(N);
+    std::vector<int32_t> tri(3 * T), we(2 * E), wid(E);
+    int64_t n0 = 0, t0 = 0, e0 = 0;
+    for (int32_t k = 0; k < n_meshes; ++k) {
+        const felbm_mesh_desc& d = meshes[k];
+        std::copy(d.xy, d.xy + 2 * (size_t)d.n_nodes, xy.begin() + 2 * n0);
+        std::fill(npx.begin() + n0, npx.begin() + n0 + d.n_nodes, d.period_x);
+        std::fill(npy.begin() + n0, npy.begin() + n0 + d.n_nodes, d.period_y);
+        for (int64_t i = 0; i < 3LL * d.n_tri; ++i) {
+            if (d.tri[i] < 0 || d.tri[i] >= d.n_nodes) {
+                felbm::set_error("felbm_mesh_create_batch: triangle node id out of range");
+                return FELBM_ERR_INVALID_ARG;
+            }
+            tri[3 * t0 + i] = (int32_t)(d.tri[i] + n0);
+        }
+        for (int64_t i = 0; i < 2LL * d.n_wall_edges; ++i) {
+            if (d.wall_edges[i] < 0 || d.wall_edges[i] >= d.n_nodes) {
+                felbm::set_error("felbm_mesh_create_batch: wall edge node id out of range");
+                return FELBM_ERR_INVALID_ARG;
+            }
+            we[2 * e0 + i] = (int32_t)(d.wall_edges[i] + n0);
+        }
+        std::copy(d.wall_id, d.wall_id + d.n_wall_edges, wid.begin() + e0);
+        n0 += d.n_nodes;
+        t0 += d.n_tri;
+        e0 += d.n_wall_edges;
+    }
+    felbm_mesh* m = new (std::nothrow) felbm_mesh;
+    if (!m) {
+        felbm::set_error("felbm_mesh_create_batch: out of host memory");
+        return FELBM_ERR_INVALID_ARG;
+    }
+    int rc;
+    try {
+        rc = felbm::build_mesh(xy.data(), (int32_t)N, tri.data(), (int32_t)T, E ? we.data() : nullptr,
+                               E ? wid.data() : nullptr, (int32_t)E, npx, npy, m->h);
+    } catch (const std::exception& ex) {
+        felbm::set_error(std::string("felbm_mesh_create_batch: ") + ex.what());
         rc = FELBM_ERR_INVALID_ARG;
     }
     if (rc != FELBM_OK) {
@@ -451,11 +634,25 @@ int felbm_mesh_info_get(const felbm_mesh* mesh, felbm_mesh_info* out) {
     out->n_nodes = m.N;
     out->n_tri = m.T;
     out->n_wall_edges = m.E;
+    out->n_groups = m.G;
     out->nnz = m.row_ptr.empty() ? 0 : m.row_ptr[m.N];
     out->max_degree = m.max_degree;
     out->bandwidth = m.bandwidth;
     out->min_area = m.min_area;
     out->total_area = m.total_area;
+    return FELBM_OK;
+}
+
+int felbm_mesh_groups(const felbm_mesh* mesh, int32_t* group_first_node, int32_t* group_nodes) {
+    if (!mesh) {
+        felbm::set_error("felbm_mesh_groups: invalid argument");
+        return FELBM_ERR_INVALID_ARG;
+    }
+    const felbm::HostMesh& m = mesh->h;
+    for (int32_t g = 0; g < m.G; ++g) {
+        if (group_first_node) group_first_node[g] = m.grp_first_caller[g];
+        if (group_nodes) group_nodes[g] = m.grp_size[g];
+    }
     return FELBM_OK;
 }
 

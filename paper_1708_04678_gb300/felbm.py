@@ -15,7 +15,7 @@ import numpy as np
 
 from . import build as _build
 
-MAX_WALL_IDS = 8
+MAX_WALL_IDS = 256
 LAP_CONSISTENT, LAP_PAPER = 0, 1
 FP64, FP32_DEV = 0, 1
 SOLVER_MIXED, SOLVER_FP64 = 0, 1
@@ -44,9 +44,15 @@ class Params(ctypes.Structure):
 
 class MeshInfo(ctypes.Structure):
     _fields_ = [("n_nodes", ctypes.c_int32), ("n_tri", ctypes.c_int32),
-                ("n_wall_edges", ctypes.c_int32), ("nnz", ctypes.c_int32),
+                ("n_wall_edges", ctypes.c_int32), ("n_groups", ctypes.c_int32), ("nnz", ctypes.c_int32),
                 ("max_degree", ctypes.c_int32), ("bandwidth", ctypes.c_int32),
                 ("min_area", ctypes.c_double), ("total_area", ctypes.c_double)]
+
+
+class MeshDesc(ctypes.Structure):
+    _fields_ = [("xy", ctypes.c_void_p), ("n_nodes", ctypes.c_int32), ("tri", ctypes.c_void_p),
+                ("n_tri", ctypes.c_int32), ("wall_edges", ctypes.c_void_p), ("wall_id", ctypes.c_void_p),
+                ("n_wall_edges", ctypes.c_int32), ("period_x", ctypes.c_double), ("period_y", ctypes.c_double)]
 
 
 class DiagRequest(ctypes.Structure):
@@ -77,6 +83,16 @@ class StepTiming(ctypes.Structure):
         return {name: getattr(self, name) for name, _ in self._fields_}
 
 
+class TuneResult(ctypes.Structure):
+    _fields_ = [("cta_max_nodes", ctypes.c_int32), ("n_candidates", ctypes.c_int32),
+                ("candidates", ctypes.c_int32 * 16), ("step_ms", ctypes.c_float * 16)]
+
+    def as_dict(self):
+        n = self.n_candidates
+        return {"cta_max_nodes": self.cta_max_nodes,
+                "candidates": list(self.candidates[:n]), "step_ms": list(self.step_ms[:n])}
+
+
 _LIB = None
 _P = ctypes.c_void_p
 _I32 = ctypes.c_int32
@@ -91,6 +107,9 @@ def _declare(lib):
                                              ctypes.c_double, ctypes.POINTER(_P)]),
         "felbm_mesh_info_get": (ctypes.c_int, [_P, ctypes.POINTER(MeshInfo)]),
         "felbm_mesh_destroy": (None, [_P]),
+        "felbm_mesh_groups": (ctypes.c_int, [_P, _P, _P]),
+        "felbm_mesh_create_batch": (ctypes.c_int, [_I32, ctypes.POINTER(MeshDesc), ctypes.POINTER(_P)]),
+        "felbm_diagnostics_groups": (ctypes.c_int, [_P, _P, _I32, _P]),
         "felbm_workspace_bytes": (ctypes.c_int, [_P, ctypes.POINTER(Params),
                                                  ctypes.POINTER(ctypes.c_size_t)]),
         "felbm_init": (ctypes.c_int, [_P, ctypes.POINTER(Params), _P, _P, ctypes.c_size_t, _P,
@@ -102,6 +121,8 @@ def _declare(lib):
         "felbm_get_fields": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
         "felbm_mass_solve": (ctypes.c_int, [_P, _P, _P, _I32]),
         "felbm_mass_solve_static": (ctypes.c_int, [_P, _P, _P, _I32]),
+        "felbm_batch_schedule": (ctypes.c_int, [_P, _I32]),
+        "felbm_autotune": (ctypes.c_int, [_P, _I32, ctypes.POINTER(TuneResult)]),
         "felbm_timing_enable": (ctypes.c_int, [_P, _I32]),
         "felbm_timing_get": (ctypes.c_int, [_P, ctypes.POINTER(StepTiming)]),
         "felbm_state_destroy": (None, [_P]),
@@ -180,10 +201,45 @@ class Mesh:
     def from_dict(cls, m):
         return cls(m["xy"], m["tri"], m["wall_edges"], m["wall_id"], m["period"])
 
+    @classmethod
+    def batch(cls, meshes):
+        """felbm_mesh_create_batch over mesh dicts (xy, tri, wall_edges,
+        wall_id, period); each member keeps its periodic lengths."""
+        keep = []
+        descs = (MeshDesc * len(meshes))()
+        n_total = 0
+        for k, m in enumerate(meshes):
+            xy = np.ascontiguousarray(m["xy"], dtype=np.float64)
+            tri = np.ascontiguousarray(m["tri"], dtype=np.int32)
+            we = np.ascontiguousarray(m["wall_edges"], dtype=np.int32).reshape(-1, 2)
+            wid = np.ascontiguousarray(m["wall_id"], dtype=np.int32).reshape(-1)
+            keep += [xy, tri, we, wid]
+            d = descs[k]
+            d.xy, d.n_nodes, d.tri, d.n_tri = xy.ctypes.data, len(xy), tri.ctypes.data, len(tri)
+            d.wall_edges = we.ctypes.data if len(we) else None
+            d.wall_id = wid.ctypes.data if len(wid) else None
+            d.n_wall_edges = len(we)
+            d.period_x, d.period_y = float(m["period"][0]), float(m["period"][1])
+            n_total += len(xy)
+        self = cls.__new__(cls)
+        h = _P()
+        _check(lib().felbm_mesh_create_batch(len(meshes), descs, ctypes.byref(h)))
+        self.handle = h
+        self.n_nodes = n_total
+        return self
+
     def info(self):
         i = MeshInfo()
         _check(lib().felbm_mesh_info_get(self.handle, ctypes.byref(i)))
         return {name: getattr(i, name) for name, _ in i._fields_}
+
+    def groups(self):
+        """(first caller node id, node count) of each connected component."""
+        n = self.info()["n_groups"]
+        first = np.empty(n, dtype=np.int32)
+        size = np.empty(n, dtype=np.int32)
+        _check(lib().felbm_mesh_groups(self.handle, _ptr(first), _ptr(size)))
+        return first, size
 
     def workspace_bytes(self, params):
         n = ctypes.c_size_t()
@@ -230,6 +286,7 @@ class State:
         _check(lib().felbm_init(mesh.handle, ctypes.byref(params), _ptr(C0), workspace.data_ptr(),
                                 nbytes, ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h)))
         self.handle = h
+        self.n_groups = mesh.info()["n_groups"]
 
     def step(self, n=1):
         _check(lib().felbm_step(self.handle, int(n)))
@@ -244,6 +301,26 @@ class State:
         if code not in (0, -5):
             _check(code)
         return d.as_dict()
+
+    def diagnostics_groups(self, requests=None, n_groups=None):
+        """Per-group diagnostics; requests: list of dicts with centre, radius,
+        band, substrate (or None)."""
+        if n_groups is None:
+            n_groups = len(requests) if requests is not None else self.n_groups
+        reqs = None
+        if requests is not None:
+            reqs = (DiagRequest * n_groups)()
+            for g, r in enumerate(requests):
+                c = r.get("centre", (0.0, 0.0))
+                reqs[g].centre[0], reqs[g].centre[1] = float(c[0]), float(c[1])
+                reqs[g].radius = float(r.get("radius", 0.0))
+                reqs[g].band = float(r.get("band", 0.0))
+                reqs[g].substrate_wall_id = int(r.get("substrate", 0))
+        out = (Diag * n_groups)()
+        code = lib().felbm_diagnostics_groups(self.handle, reqs, n_groups, out)
+        if code not in (0, -5):
+            _check(code)
+        return [o.as_dict() for o in out]
 
     def get_state(self, g=None, h=None):
         if g is None:
@@ -276,6 +353,14 @@ class State:
         float64, caller order; enqueued on the state's stream."""
         k = d_B.shape[0] if k is None else k
         _check(lib().felbm_mass_solve_static(self.handle, d_B.data_ptr(), d_X.data_ptr(), int(k)))
+
+    def batch_schedule(self, cta_max_nodes):
+        _check(lib().felbm_batch_schedule(self.handle, int(cta_max_nodes)))
+
+    def autotune(self, trials=5):
+        r = TuneResult()
+        _check(lib().felbm_autotune(self.handle, int(trials), ctypes.byref(r)))
+        return r.as_dict()
 
     def timing_enable(self, on=True):
         _check(lib().felbm_timing_enable(self.handle, 1 if on else 0))

@@ -41,6 +41,7 @@ __all__ = [
     "rough_wall_droplet",
     "small_sessile",
     "small_free_droplet",
+    "batch",
 ]
 
 
@@ -264,6 +265,39 @@ def droplet_sweep(seed=2, count=64, w_min=64, w_max=512, jitter=0.2, steps=5000)
                     "mesh": mesh, "C0": C0, "phys": phys, "steps": steps,
                     "centre": centre, "R": R})
     return out
+
+
+def batch(workloads):
+    """Many independent sessile workloads as one batch: member k keeps its
+    mesh (and periodic width) and gets wall ids 2k (bottom) and 2k+1 (top),
+    so theta_deg lists the angles of all walls; C0 is concatenated.  The
+    members must share every physical parameter except the contact angles.
+    Returns the batch workload with ``meshes`` (for Mesh.batch) and the
+    per-member ``members`` (offset, node count, centre, R)."""
+    meshes, thetas, C0, members = [], [], [], []
+    ref = dict(workloads[0]["phys"])
+    off = 0
+    for k, w in enumerate(workloads):
+        m = dict(w["mesh"])
+        ids = np.asarray(m["wall_id"], dtype=np.int32)
+        if ids.size and ids.max() > 1:
+            raise ValueError("batch members must use wall ids 0 and 1")
+        m["wall_id"] = (ids + 2 * k).astype(np.int32)
+        meshes.append(m)
+        th = tuple(w["phys"]["theta_deg"]) + (90.0,) * (2 - len(w["phys"]["theta_deg"]))
+        thetas.extend(th[:2])
+        for key in ("dt", "tau_l", "tau_v", "rho_l", "rho_v", "sigma", "xi", "mobility"):
+            if w["phys"][key] != ref[key]:
+                raise ValueError(f"batch members differ in {key}")
+        C0.append(w["C0"])
+        n = len(m["xy"])
+        members.append({"offset": off, "nodes": n, "centre": w["centre"], "R": w["R"],
+                        "substrate": 2 * k, "name": w["name"]})
+        off += n
+    phys = dict(ref)
+    phys["theta_deg"] = tuple(thetas)
+    return {"name": f"batch of {len(workloads)} droplets", "meshes": meshes, "C0": np.concatenate(C0),
+            "phys": phys, "members": members, "steps": max(w["steps"] for w in workloads)}
 
 
 def rough_wall_droplet(seed=4, width=2048, height=1024, rows=1017, R=300.0,
