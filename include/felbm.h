@@ -293,6 +293,35 @@ int felbm_mass_solve(felbm_state* state, const double* B, double* X, int32_t k);
  * or events).  They may overlap with felbm_step, which does not touch it. */
 int felbm_mass_solve_static(felbm_state* state, const double* d_B, double* d_X, int32_t k);
 
+/* ---------------------------------------------------------------- adjoint
+ * Reverse-mode derivatives of felbm_step for FELBM_FP64 states (NEXT-1 of the
+ * build's plan; the paper has no adjoint).  With lambda = dL/dpsi^{n+1}
+ * seeded, felbm_adjoint_step maps it to dL/dpsi^n using the CURRENT state as
+ * psi^n (restore it with felbm_checkpoint_load / felbm_set_state first) and
+ * adds (d psi^{n+1}/d phi_c)^T lambda to the wetting-potential gradient.  The
+ * reverse of each part of the step: the mass solve (M11 is symmetric: the
+ * same solver), the element residuals and the node gathers (transposed as
+ * gathers, no atomics), the P0 forces and the collision (Jacobians by
+ * forward-mode dual numbers), the chemical potential with its wetting flux,
+ * and the moments.  Enqueued on the state's stream; does not synchronise. */
+int felbm_adjoint_seed(felbm_state* state, const double* dL_dg, const double* dL_dh);  /* host [9][N] each */
+int felbm_adjoint_step(felbm_state* state);
+/* Copy lambda (= dL/dpsi of the state the last adjoint step was taken at;
+ * either pointer pair may be NULL) and the accumulated dL/dphi_c per wall id
+ * ([n_wall_ids] or NULL) to the host.  Synchronises. */
+int felbm_adjoint_get(felbm_state* state, double* dL_dg, double* dL_dh, double* dL_dphi_c);
+
+/* Replace the wetting potentials phi_c[0..n_wall_ids) of a state (e.g. between
+ * runs of a gradient check); takes effect at the next step.  Synchronises. */
+int felbm_set_wetting(felbm_state* state, const double* phi_c, int32_t n_wall_ids);
+
+/* Device-to-device snapshots of the state (the checkpoints of the adjoint's
+ * recomputation): d_buf is a caller-owned device buffer of
+ * felbm_checkpoint_bytes.  Enqueued on the state's stream. */
+int felbm_checkpoint_bytes(const felbm_state* state, size_t* bytes);
+int felbm_checkpoint_save(felbm_state* state, void* d_buf);
+int felbm_checkpoint_load(felbm_state* state, const void* d_buf);
+
 /* Device time of the phases of one time step, milliseconds, from CUDA events
  * recorded inside the step's graph (instrumentation, not part of the method). */
 typedef struct felbm_step_timing {

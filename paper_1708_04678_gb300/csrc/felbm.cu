@@ -82,6 +82,7 @@ struct DevMesh {
     const float* area32;      // [Tp]   FP32 copies for the FP32-deviation path
     const float* grad32;      // [6][Tp]
     const int32_t* nbr;       // [3][Tp]
+    const int32_t* nbr_slot;  // [3][Tp] local index of the shared edge in the neighbour
     const int32_t* row_ptr;   // [N+1]
     const int32_t* col;       // [nnz]
     const double* mval;       // [nnz] consistent mass
@@ -450,6 +451,7 @@ __global__ void __launch_bounds__(128) k_cheb(DevMesh m, Bufs b, const double* _
 enum Final { kStore = 0, kAddPsi = 1, kAddX64 = 2, kUpdateDev = 3 };
 
 #include "felbm_dev32.cuh"
+#include "felbm_adjoint.cuh"
 
 template <int kFinal>
 __global__ void __launch_bounds__(128) k_cheb32(DevMesh m, Phys c, Bufs b, const float* __restrict__ cur,
@@ -942,6 +944,7 @@ struct felbm_state {
     bool dev32 = false;   // FELBM_FP32_DEV storage
     bool use_pdl = true;  // programmatic dependent launch between solve sweeps
     felbm::GroupTables gt{};
+    felbm::AdjBufs adj{};         // adjoint buffers (FP64 states)
     std::vector<double> gmass0;   // per-group mass at felbm_init
     // batch schedule (FP32_DEV): groups of at most cta_max_nodes nodes run one
     // CTA each (k_step_cta32); the rest, a prefix of the node and triangle
@@ -966,7 +969,7 @@ static int ell_width(const HostMesh& h) {
 
 // Layout of the workspace; with base == nullptr only the size is computed.
 static size_t carve(const HostMesh& h, bool dev32, void* base, DevMesh* dm, Bufs* b,
-                    GroupTables* gtab = nullptr) {
+                    GroupTables* gtab = nullptr, AdjBufs* adj = nullptr) {
     Carver cv(base);
     size_t Np = pad64(h.N), Tp = pad64(h.T);
     size_t nnz = h.row_ptr[h.N], ninc = h.inc_ptr[h.N], nwinc = h.winc_ptr[h.N];
@@ -978,6 +981,7 @@ static size_t carve(const HostMesh& h, bool dev32, void* base, DevMesh* dm, Bufs
     d.area32 = cv.take<float>(Tp);
     d.grad32 = cv.take<float>(6 * Tp);
     d.nbr = cv.take<int32_t>(3 * Tp);
+    d.nbr_slot = cv.take<int32_t>(3 * Tp);
     d.row_ptr = cv.take<int32_t>(h.N + 1);
     d.col = cv.take<int32_t>(nnz);
     d.mval = cv.take<double>(nnz);
@@ -1053,6 +1057,22 @@ static size_t carve(const HostMesh& h, bool dev32, void* base, DevMesh* dm, Bufs
     g.out = cv.take<double>(G * kDiagSlots);
     g.cta_groups = cv.take<int32_t>(G);
     if (gtab) *gtab = g;
+    AdjBufs ad{};
+    if (!dev32) {
+        ad.lam = cv.take<double>(18 * Np);
+        ad.lamhat = cv.take<double>(18 * Np);
+        ad.lamR = cv.take<double>(18 * (size_t)h.T);
+        ad.lamE = cv.take<double>(9 * (size_t)h.T);
+        ad.lamG = cv.take<double>(2 * Tp);
+        ad.lamMu = cv.take<double>(Np);
+        ad.lamC = cv.take<double>(Np);
+        ad.lamP = cv.take<double>(Np);
+        ad.lamUx = cv.take<double>(Np);
+        ad.lamUy = cv.take<double>(Np);
+        ad.dphi = cv.take<double>(E);
+        ad.kval = cv.take<double>(nnz);
+    }
+    if (adj) *adj = ad;
     if (dm) {
         d.N = h.N;
         d.T = h.T;
@@ -1308,7 +1328,7 @@ int felbm_init(const felbm_mesh* mesh, const felbm_params* params, const double*
     st->prm = *params;
     st->stream = static_cast<cudaStream_t>(stream);
     st->dev32 = dev32;
-    carve(h, dev32, d_workspace, &st->dm, &st->buf, &st->gt);
+    carve(h, dev32, d_workspace, &st->dm, &st->buf, &st->gt, &st->adj);
     Phys& ph = st->phys;
     ph.dt = params->dt;
     ph.tau_l = params->tau_l;
@@ -1382,7 +1402,7 @@ int felbm_init(const felbm_mesh* mesh, const felbm_params* params, const double*
                       outv.begin() + (size_t)r * st->dm.Tp);
         return outv;
     };
-    std::vector<int32_t> tri_p = pad_tri(h.tri, 3), nbr_p = pad_tri(h.nbr, 3);
+    std::vector<int32_t> tri_p = pad_tri(h.tri, 3), nbr_p = pad_tri(h.nbr, 3), slot_p = pad_tri(h.nbr_slot, 3);
     std::vector<double> grad_p = pad_trid(h.grad, 6), area_p = pad_trid(h.area, 1);
     std::vector<float> grad32_p(grad_p.begin(), grad_p.end()), area32_p(area_p.begin(), area_p.end());
     std::vector<float> inc_bx32(h.inc_bx.begin(), h.inc_bx.end()), inc_by32(h.inc_by.begin(), h.inc_by.end());
@@ -1402,6 +1422,7 @@ int felbm_init(const felbm_mesh* mesh, const felbm_params* params, const double*
     UP(d.grad32, grad32_p);
     UP(d.area32, area32_p);
     UP(d.nbr, nbr_p);
+    UP(d.nbr_slot, slot_p);
     UP(d.row_ptr, h.row_ptr);
     UP(d.col, h.col);
     UP(d.mval, h.mass);
@@ -1438,6 +1459,7 @@ int felbm_init(const felbm_mesh* mesh, const felbm_params* params, const double*
     UP(st->gt.tri_end, h.grp_tri_end);
     UP(st->gt.wall_ptr, h.grp_wall_ptr);
     UP(st->gt.wall_edge, h.grp_wall_edge);
+    if (!dev32) UP(st->adj.kval, h.stiff);
 #undef UP
     if (e != cudaSuccess) return fail(e, "felbm_init: upload");
     e = cudaMemcpyAsync(st->buf.stage, C0, sizeof(double) * h.N, cudaMemcpyHostToDevice, s);
@@ -2003,6 +2025,158 @@ int felbm_autotune(felbm_state* st, int32_t trials, felbm_tune_result* out) {
     if (rc2) return rc2;
     out->cta_max_nodes = best_t;
     return felbm_batch_schedule(st, best_t);
+}
+
+// ------------------------------------------------------------- adjoint ----
+int felbm_set_wetting(felbm_state* st, const double* phi_c, int32_t n_wall_ids) {
+    if (!st || !phi_c || n_wall_ids < 1 || n_wall_ids > FELBM_MAX_WALL_IDS) {
+        set_error("felbm_set_wetting: invalid argument");
+        return FELBM_ERR_INVALID_ARG;
+    }
+    const HostMesh& h = st->hm;
+    std::vector<double> wall_phi(std::max<int32_t>(h.E, 1), 0.0);
+    for (int32_t e = 0; e < h.E; ++e) {
+        if (h.wall_id[e] >= n_wall_ids) {
+            set_error("felbm_set_wetting: a wall id has no phi_c");
+            return FELBM_ERR_INVALID_ARG;
+        }
+        wall_phi[e] = phi_c[h.wall_id[e]];
+    }
+    for (int32_t k = 0; k < n_wall_ids; ++k) st->prm.phi_c[k] = phi_c[k];
+    if (h.E > 0)
+        FELBM_CUDA(cudaMemcpyAsync(const_cast<double*>(st->dm.wall_phi), wall_phi.data(), sizeof(double) * h.E,
+                                   cudaMemcpyHostToDevice, st->stream));
+    FELBM_CUDA(cudaStreamSynchronize(st->stream));
+    return FELBM_OK;
+}
+
+int felbm_checkpoint_bytes(const felbm_state* st, size_t* bytes) {
+    if (!st || !bytes) {
+        set_error("felbm_checkpoint_bytes: invalid argument");
+        return FELBM_ERR_INVALID_ARG;
+    }
+    *bytes = st->dev32 ? (size_t)st->dm.Np * (18 * sizeof(float) + sizeof(double) + 3 * sizeof(float))
+                       : (size_t)st->dm.Np * 18 * sizeof(double);
+    return FELBM_OK;
+}
+
+static int checkpoint_copy(felbm_state* st, void* dst_v, const void* src_v, bool save) {
+    const DevMesh& m = st->dm;
+    const Bufs& b = st->buf;
+    char* ck = reinterpret_cast<char*>(save ? dst_v : const_cast<void*>(src_v));
+    std::vector<std::pair<void*, size_t>> parts;
+    if (st->dev32) {
+        parts = {{b.dpsi, 18 * (size_t)m.Np * sizeof(float)}, {b.C, (size_t)m.Np * sizeof(double)},
+                 {b.p32, (size_t)m.Np * sizeof(float)}, {b.ux32, (size_t)m.Np * sizeof(float)},
+                 {b.uy32, (size_t)m.Np * sizeof(float)}};
+    } else {
+        parts = {{b.psi, 18 * (size_t)m.Np * sizeof(double)}};
+    }
+    size_t off = 0;
+    for (auto& pr : parts) {
+        void* d = save ? (void*)(ck + off) : pr.first;
+        const void* sr = save ? (const void*)pr.first : (const void*)(ck + off);
+        FELBM_CUDA(cudaMemcpyAsync(d, sr, pr.second, cudaMemcpyDeviceToDevice, st->stream));
+        off += pr.second;
+    }
+    return FELBM_OK;
+}
+
+int felbm_checkpoint_save(felbm_state* st, void* d_dst) {
+    if (!st || !d_dst) {
+        set_error("felbm_checkpoint_save: invalid argument");
+        return FELBM_ERR_INVALID_ARG;
+    }
+    return checkpoint_copy(st, d_dst, nullptr, true);
+}
+
+int felbm_checkpoint_load(felbm_state* st, const void* d_src) {
+    if (!st || !d_src) {
+        set_error("felbm_checkpoint_load: invalid argument");
+        return FELBM_ERR_INVALID_ARG;
+    }
+    return checkpoint_copy(st, nullptr, d_src, false);
+}
+
+int felbm_adjoint_seed(felbm_state* st, const double* dL_dg, const double* dL_dh) {
+    if (!st || !dL_dg || !dL_dh) {
+        set_error("felbm_adjoint_seed: invalid argument");
+        return FELBM_ERR_INVALID_ARG;
+    }
+    if (st->dev32) {
+        set_error("felbm_adjoint_seed: the adjoint is available for FELBM_FP64 states");
+        return FELBM_ERR_UNSUPPORTED;
+    }
+    cudaStream_t s = st->stream;
+    const int N = st->dm.N;
+    FELBM_CUDA(cudaMemcpyAsync(st->buf.stage, dL_dg, sizeof(double) * 9 * N, cudaMemcpyHostToDevice, s));
+    FELBM_CUDA(cudaMemcpyAsync(st->buf.stage + (size_t)9 * N, dL_dh, sizeof(double) * 9 * N, cudaMemcpyHostToDevice, s));
+    k_scatter_in<<<grid_for(N, kBlock), kBlock, 0, s>>>(st->dm, st->buf.stage, st->adj.lam, 18);
+    FELBM_CUDA(cudaGetLastError());
+    if (st->hm.E > 0) FELBM_CUDA(cudaMemsetAsync(st->adj.dphi, 0, sizeof(double) * st->hm.E, s));
+    FELBM_CUDA(cudaStreamSynchronize(s));
+    return FELBM_OK;
+}
+
+int felbm_adjoint_step(felbm_state* st) {
+    if (!st) {
+        set_error("felbm_adjoint_step: invalid argument");
+        return FELBM_ERR_INVALID_ARG;
+    }
+    if (st->dev32) {
+        set_error("felbm_adjoint_step: the adjoint is available for FELBM_FP64 states");
+        return FELBM_ERR_UNSUPPORTED;
+    }
+    cudaStream_t s = st->stream;
+    const DevMesh& m = st->dm;
+    Bufs& b = st->buf;
+    AdjBufs& a = st->adj;
+    // fields of the state psi^n (the input of the step being reversed)
+    k_collide<<<grid_for(m.N, kBlock), kBlock, 0, s>>>(m, st->phys, b, 0);
+    k_mu<<<grid_for(m.N, kBlock), kBlock, 0, s>>>(m, st->phys, b);
+    k_gradmu<<<grid_for(m.T, kBlock), kBlock, 0, s>>>(m, b);
+    // lambda_RHS = M11^{-1} lambda with the step's solver
+    FELBM_CUDA(cudaMemcpyAsync(b.rhs, a.lam, sizeof(double) * 18 * m.Np, cudaMemcpyDeviceToDevice, s));
+    if (st->mode == FELBM_SOLVER_FP64)
+        k_cheb_start<false><<<grid_for(m.N, kBlock), kBlock, 0, s>>>(m, b, st->inv_theta);
+    else
+        k_cheb_start<true><<<grid_for(m.N, kBlock), kBlock, 0, s>>>(m, b, st->inv_theta);
+    a.lamRHS = enqueue_solve(st, m, b, s, false);
+    k_adj_elem_a<<<grid_for(m.T, 128), 128, 0, s>>>(m, st->phys, b, a);
+    k_adj_elem_b<<<grid_for(m.T, kBlock), kBlock, 0, s>>>(m, a);
+    k_adj_node_d<<<grid_for(m.N, 128), 128, 0, s>>>(m, st->phys, a);
+    k_adj_node_e<<<grid_for(m.N, 128), 128, 0, s>>>(m, st->phys, b, a);
+    FELBM_CUDA(cudaGetLastError());
+    return FELBM_OK;
+}
+
+int felbm_adjoint_get(felbm_state* st, double* dL_dg, double* dL_dh, double* dL_dphi_c) {
+    if (!st || (!dL_dg != !dL_dh)) {
+        set_error("felbm_adjoint_get: invalid argument");
+        return FELBM_ERR_INVALID_ARG;
+    }
+    if (st->dev32) {
+        set_error("felbm_adjoint_get: the adjoint is available for FELBM_FP64 states");
+        return FELBM_ERR_UNSUPPORTED;
+    }
+    cudaStream_t s = st->stream;
+    const int N = st->dm.N;
+    if (dL_dg) {
+        k_gather_out<<<grid_for(N, kBlock), kBlock, 0, s>>>(st->dm, st->adj.lam, st->buf.stage, 18);
+        FELBM_CUDA(cudaGetLastError());
+        FELBM_CUDA(cudaMemcpyAsync(dL_dg, st->buf.stage, sizeof(double) * 9 * N, cudaMemcpyDeviceToHost, s));
+        FELBM_CUDA(cudaMemcpyAsync(dL_dh, st->buf.stage + (size_t)9 * N, sizeof(double) * 9 * N,
+                                   cudaMemcpyDeviceToHost, s));
+    }
+    std::vector<double> de(std::max<int32_t>(st->hm.E, 1));
+    if (st->hm.E > 0)
+        FELBM_CUDA(cudaMemcpyAsync(de.data(), st->adj.dphi, sizeof(double) * st->hm.E, cudaMemcpyDeviceToHost, s));
+    FELBM_CUDA(cudaStreamSynchronize(s));
+    if (dL_dphi_c) {
+        for (int k = 0; k < st->prm.n_wall_ids; ++k) dL_dphi_c[k] = 0.0;
+        for (int32_t e = 0; e < st->hm.E; ++e) dL_dphi_c[st->hm.wall_id[e]] += de[e];   // edge order: fixed
+    }
+    return FELBM_OK;
 }
 
 void felbm_state_destroy(felbm_state* st) {

@@ -23,6 +23,7 @@ struct HostMesh {
     std::vector<double> area;                 // [T]
     std::vector<double> grad;                 // [6][T]: bx0, by0, bx1, by1, bx2, by2
     std::vector<int32_t> nbr;                 // [3][T]: triangle across the edge opposite vertex k, -1 = wall
+    std::vector<int32_t> nbr_slot;            // [3][T]: that edge's local index in the neighbour
     // node-node pattern (CSR, sorted columns, diagonal included)
     std::vector<int32_t> row_ptr, col;
     std::vector<double> mass;                 // consistent mass matrix entries

@@ -163,7 +163,7 @@ static int build_mesh(const double* xy, int32_t N, const int32_t* tri_in, int32_
     }
 
     // ---- edges: neighbours across each edge, open edges must be walls ----
-    std::vector<int32_t> nbr_old(3 * (size_t)T, -1);
+    std::vector<int32_t> nbr_old(3 * (size_t)T, -1), slot_old(3 * (size_t)T, -1);
     std::unordered_map<uint64_t, int64_t> open;
     open.reserve((size_t)T * 2);
     auto key = [](int32_t a, int32_t b) {
@@ -188,7 +188,9 @@ static int build_mesh(const double* xy, int32_t N, const int32_t* tri_in, int32_
                     return FELBM_ERR_BAD_MESH;
                 }
                 nbr_old[3 * t + k] = (int32_t)(o / 3);
+                slot_old[3 * t + k] = (int32_t)(o % 3);
                 nbr_old[o] = t;
+                slot_old[o] = k;
                 it->second = -1;  // closed
             }
         }
@@ -300,6 +302,7 @@ static int build_mesh(const double* xy, int32_t N, const int32_t* tri_in, int32_
     m.area.assign(T, 0.0);
     m.grad.assign(6 * (size_t)T, 0.0);
     m.nbr.assign(3 * (size_t)T, -1);
+    m.nbr_slot.assign(3 * (size_t)T, -1);
     for (int32_t t = 0; t < T; ++t) {
         int32_t o = torder[t];
         double A = area[o];
@@ -308,6 +311,7 @@ static int build_mesh(const double* xy, int32_t N, const int32_t* tri_in, int32_
             m.tri[(size_t)k * T + t] = m.iperm[tri_in[3 * o + k]];
             int32_t nb = nbr_old[3 * o + k];
             m.nbr[(size_t)k * T + t] = nb < 0 ? -1 : tnew[nb];
+            m.nbr_slot[(size_t)k * T + t] = slot_old[3 * o + k];
             // gradient of the P1 shape function of local vertex k
             int j = (k + 1) % 3, l = (k + 2) % 3;
             m.grad[(size_t)(2 * k) * T + t] = (ly[3 * o + j] - ly[3 * o + l]) / (2.0 * A);

@@ -121,6 +121,13 @@ def _declare(lib):
         "felbm_get_fields": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
         "felbm_mass_solve": (ctypes.c_int, [_P, _P, _P, _I32]),
         "felbm_mass_solve_static": (ctypes.c_int, [_P, _P, _P, _I32]),
+        "felbm_adjoint_seed": (ctypes.c_int, [_P, _P, _P]),
+        "felbm_adjoint_step": (ctypes.c_int, [_P]),
+        "felbm_adjoint_get": (ctypes.c_int, [_P, _P, _P, _P]),
+        "felbm_set_wetting": (ctypes.c_int, [_P, _P, _I32]),
+        "felbm_checkpoint_bytes": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_size_t)]),
+        "felbm_checkpoint_save": (ctypes.c_int, [_P, _P]),
+        "felbm_checkpoint_load": (ctypes.c_int, [_P, _P]),
         "felbm_batch_schedule": (ctypes.c_int, [_P, _I32]),
         "felbm_autotune": (ctypes.c_int, [_P, _I32, ctypes.POINTER(TuneResult)]),
         "felbm_timing_enable": (ctypes.c_int, [_P, _I32]),
@@ -353,6 +360,38 @@ class State:
         float64, caller order; enqueued on the state's stream."""
         k = d_B.shape[0] if k is None else k
         _check(lib().felbm_mass_solve_static(self.handle, d_B.data_ptr(), d_X.data_ptr(), int(k)))
+
+    # -- adjoint and checkpoints ------------------------------------------
+    def set_wetting(self, phi_c):
+        phi = np.ascontiguousarray(phi_c, dtype=np.float64)
+        _check(lib().felbm_set_wetting(self.handle, _ptr(phi), int(phi.size)))
+
+    def checkpoint_bytes(self):
+        n = ctypes.c_size_t()
+        _check(lib().felbm_checkpoint_bytes(self.handle, ctypes.byref(n)))
+        return n.value
+
+    def checkpoint_save(self, d_buf):
+        _check(lib().felbm_checkpoint_save(self.handle, d_buf.data_ptr()))
+
+    def checkpoint_load(self, d_buf):
+        _check(lib().felbm_checkpoint_load(self.handle, d_buf.data_ptr()))
+
+    def adjoint_seed(self, dL_dg, dL_dh):
+        dg = np.ascontiguousarray(dL_dg, dtype=np.float64)
+        dh = np.ascontiguousarray(dL_dh, dtype=np.float64)
+        _check(lib().felbm_adjoint_seed(self.handle, _ptr(dg), _ptr(dh)))
+
+    def adjoint_step(self):
+        _check(lib().felbm_adjoint_step(self.handle))
+
+    def adjoint_get(self, n_wall_ids=None):
+        n_ids = self.params.n_wall_ids if n_wall_ids is None else n_wall_ids
+        dg = np.empty((9, self.N))
+        dh = np.empty((9, self.N))
+        dphi = np.zeros(max(n_ids, 1))
+        _check(lib().felbm_adjoint_get(self.handle, _ptr(dg), _ptr(dh), _ptr(dphi)))
+        return dg, dh, dphi[:n_ids]
 
     def batch_schedule(self, cta_max_nodes):
         _check(lib().felbm_batch_schedule(self.handle, int(cta_max_nodes)))
