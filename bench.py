@@ -148,6 +148,21 @@ def peaks():
     return 6800.0, "fallback"
 
 
+# ------------------------------------------------------ rank aggregation --
+def max_over_ranks(x, torch, dist, world, device):
+    """The largest of the ranks' values (the job's time is its slowest rank)."""
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank_step, steps, world, max_ms):
+    """Whole-job throughput of N independent replicas: all ranks' units over
+    the slowest rank's time."""
+    return units_per_rank_step * steps * world / (max_ms * 1e-3)
+
+
 # --------------------------------------------------------------- GPU arm --
 def time_precision(F, torch, w, dev, precision, K, W, flush, barrier, world, dist):
     """Build a state of the workload in one precision, run W warm-up steps and
@@ -158,6 +173,7 @@ def time_precision(F, torch, w, dev, precision, K, W, flush, barrier, world, dis
     stream = torch.cuda.Stream(dev)
     st = F.State(mesh, prm, w["C0"], device=dev, stream=stream)
     st.timing_enable(True)
+    tune = st.autotune(trials=5)
     for k in range(W):
         with torch.cuda.stream(stream):
             flush.fill_(k & 255)
@@ -177,11 +193,7 @@ def time_precision(F, torch, w, dev, precision, K, W, flush, barrier, world, dis
         phases.append(st.timing_get())           # synchronises the stream
     torch.cuda.synchronize()
     barrier()
-    total_ms = sum(ev0[k].elapsed_time(ev1[k]) for k in range(K))
-    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    total_ms = float(t.item())
+    total_ms = max_over_ranks(sum(ev0[k].elapsed_time(ev1[k]) for k in range(K)), torch, dist, world, dev)
     diag = st.diagnostics(w["centre"], w["R"], w["phys"]["xi"])
 
     # end to end through the public API with host buffers: pinned g, h in,
@@ -201,15 +213,11 @@ def time_precision(F, torch, w, dev, precision, K, W, flush, barrier, world, dis
         st.step(1)
         st.diagnostics()
     torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
-    e = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(e, op=dist.ReduceOp.MAX)
-    e2e_s = float(e.item())
+    e2e_s = max_over_ranks(time.perf_counter() - t0, torch, dist, world, dev)
     ph = {k: statistics.mean(p[k] for p in phases) for k in phases[0] if k.endswith("_ms")}
     info = mesh.info()
     st.close()
-    return {"total_ms": total_ms, "e2e_s": e2e_s, "phase_ms": ph, "launches": phases[0]["launches"],
+    return {"total_ms": total_ms, "e2e_s": e2e_s, "phase_ms": ph, "launches": phases[0]["launches"], "tune": tune,
             "solve_launches": phases[0]["solve_launches"], "info": info, "diag": diag}
 
 
@@ -239,11 +247,7 @@ def time_batch(F, torch, dev, K, flush, barrier, world, dist):
         ev1[k].record(stream)
     torch.cuda.synchronize()
     barrier()
-    total_ms = sum(ev0[k].elapsed_time(ev1[k]) for k in range(K))
-    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    total_ms = float(t.item())
+    total_ms = max_over_ranks(sum(ev0[k].elapsed_time(ev1[k]) for k in range(K)), torch, dist, world, dev)
     reqs = [{"centre": m["centre"], "radius": m["R"], "band": 4.0, "substrate": m["substrate"]}
             for m in b["members"]]
     dg = st.diagnostics_groups(reqs)
@@ -251,7 +255,7 @@ def time_batch(F, torch, dev, K, flush, barrier, world, dist):
     st.close()
     return {"workload": "64-droplet contact-angle sweep, widths 64..512, FP32 deviation storage",
             "nodes": n, "members": len(b["members"]), "steps": K,
-            "value": n * K * world / (total_ms * 1e-3), "unit": "node-updates/s",
+            "value": job_rate(n, K, world, total_ms), "unit": "node-updates/s",
             "ms_per_step": total_ms / K, "schedule": tune,
             "finite": all(d["status"] == 0 for d in dg),
             "max_abs_mass_drift_rel": max(abs(d["mass_drift_rel"]) for d in dg)}
@@ -310,10 +314,10 @@ def run_gpu(args):
         achieved = alg_bytes / (sweep_ms * 1e-3) / 1e9
 
         def summary(r, dtype):
-            return {"value": N * K * world / (r["total_ms"] * 1e-3), "ms_per_step": r["total_ms"] / K,
+            return {"value": job_rate(N, K, world, r["total_ms"]), "ms_per_step": r["total_ms"] / K,
                     "dtype": dtype, "phase_ms": {k: round(v, 5) for k, v in r["phase_ms"].items()},
-                    "launches_per_step": r["launches"],
-                    "e2e_value": N * K * world / r["e2e_s"],
+                    "launches_per_step": r["launches"], "autotune": r["tune"],
+                    "e2e_value": job_rate(N, K, world, r["e2e_s"] * 1e3),
                     "after_timed_steps": {k: r["diag"][k] for k in ("max_u", "delta_p", "mass_drift_rel",
                                                                     "interface_rho_uu", "status")}}
 

@@ -225,18 +225,20 @@ int felbm_diagnostics(felbm_state* state, const felbm_diag_request* req, felbm_d
 int felbm_batch_schedule(felbm_state* state, int32_t cta_max_nodes);
 
 typedef struct felbm_tune_result {
-    int32_t cta_max_nodes;   /* chosen threshold (0 = tiled only) */
+    int32_t sweep_parts;     /* chosen threads per node of the FP32 solve sweeps */
+    float parts_ms[4];       /* step time with 1, 2, 3, 6 threads per node (0 = not timed) */
+    int32_t cta_max_nodes;   /* chosen batch threshold (0 = tiled only) */
     int32_t n_candidates;
     int32_t candidates[16];  /* thresholds timed */
     float step_ms[16];       /* mean device time of one step for each */
 } felbm_tune_result;
 
-/* Autotuner of the batch schedule: times `trials` steps (after one warm-up
- * step) for each distinct split of the members -- tiled only, and CTA per
- * member up to 2^11 .. 2^17 nodes -- and keeps the fastest.  The state (and
- * the step count) is saved before and restored after, so the simulation is
- * unchanged.  Synchronises.  FP64 states and one-member meshes keep the
- * tiled schedule. */
+/* Autotuner: times `trials` steps (after one warm-up step) per candidate and
+ * keeps the fastest -- first the threads per node of the FP32 solve sweeps
+ * (1, 2, 3 or 6; states with an FP32 solve and an ELL pattern), then, for
+ * FP32_DEV batches, each distinct split of the members (tiled only, CTA per
+ * member up to 2^11 .. 2^17 nodes).  The state and the step count are saved
+ * before and restored after, so the simulation is unchanged.  Synchronises. */
 int felbm_autotune(felbm_state* state, int32_t trials, felbm_tune_result* out);
 
 /* Diagnostics per group (see felbm_mesh_groups): out[g] for g < n_groups, each

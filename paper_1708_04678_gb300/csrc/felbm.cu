@@ -502,14 +502,17 @@ __device__ __forceinline__ void pdl_release() { asm volatile("griddepcontrol.lau
 // loaded up front (coalesced, column-major); for the store variant the g and
 // h halves of a node run in two threads (blockIdx.y), doubling the threads in
 // flight for this latency-bound gather.
-template <int kFinal, int kW>
+// kParts threads per node (blockIdx.y picks the part), each owning 18/kParts
+// of the node's rows; the field update needs all 18 in one thread.
+template <int kFinal, int kW, int kParts>
 __global__ void __launch_bounds__(128) k_sweep32(DevMesh m, Phys c, Bufs b, const float* __restrict__ cur,
                                                  float* prev, float a, float cc, int first, int have_x64) {
     pdl_release();
-    constexpr bool kSplit = kFinal != kUpdateDev;
-    constexpr int NQ = kSplit ? 9 : 18;
+    static_assert(kFinal != kUpdateDev || kParts == 1, "the field update needs the whole node");
+    static_assert(18 % kParts == 0, "parts must divide 18");
+    constexpr int NQ = 18 / kParts;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const int q0 = kSplit ? 9 * (int)blockIdx.y : 0;
+    const int q0 = NQ * (int)blockIdx.y;
     const int Np = m.Np;
     int col[kW];
     float val[kW];
@@ -943,6 +946,7 @@ struct felbm_state {
     cudaEvent_t ev[7] = {};
     bool dev32 = false;   // FELBM_FP32_DEV storage
     bool use_pdl = true;  // programmatic dependent launch between solve sweeps
+    int sweep_parts = 2;  // threads per node of the FP32 store sweeps (1, 2, 3, 6)
     felbm::GroupTables gt{};
     felbm::AdjBufs adj{};         // adjoint buffers (FP64 states)
     std::vector<double> gmass0;   // per-group mass at felbm_init
@@ -1134,24 +1138,50 @@ static void launch_k(bool pdl, void (*kern)(KArgs...), dim3 grid, dim3 block, cu
 
 // One FP32 Chebyshev sweep: the ELL kernel of the mesh's width, else CSR.
 // pdl: the previous launch on the stream is a sweep (a kernel that waits).
+// parts: threads per node for the store sweeps (1, 2, 3 or 6; autotuned).
+template <int kFinal, int kW>
+static void launch_sweep_w(felbm_state* st, const DevMesh& m, const Bufs& b, cudaStream_t s, const float* cur,
+                           float* prv, float a, float c, int first, int have_x64, bool pdl) {
+    const dim3 block(128);
+    const int parts = kFinal == kUpdateDev ? 1 : st->sweep_parts;
+    const dim3 grid(grid_for(m.N, 128), parts);
+    switch (parts) {
+        case 1:
+            launch_k(pdl, k_sweep32<kFinal, kW, 1>, grid, block, s, m, st->phys, b, cur, prv, a, c, first, have_x64);
+            break;
+        case 3:
+            if constexpr (kFinal != kUpdateDev)
+                launch_k(pdl, k_sweep32<kFinal, kW, 3>, grid, block, s, m, st->phys, b, cur, prv, a, c, first,
+                         have_x64);
+            break;
+        case 6:
+            if constexpr (kFinal != kUpdateDev)
+                launch_k(pdl, k_sweep32<kFinal, kW, 6>, grid, block, s, m, st->phys, b, cur, prv, a, c, first,
+                         have_x64);
+            break;
+        default:
+            if constexpr (kFinal != kUpdateDev)
+                launch_k(pdl, k_sweep32<kFinal, kW, 2>, grid, block, s, m, st->phys, b, cur, prv, a, c, first,
+                         have_x64);
+    }
+}
+
 template <int kFinal>
 static void launch_sweep(felbm_state* st, const DevMesh& m, const Bufs& b, cudaStream_t s, const float* cur,
                          float* prv, float a, float c, int first, int have_x64, bool pdl) {
-    const dim3 block(128);
-    const dim3 grid(grid_for(m.N, 128), kFinal == kUpdateDev ? 1 : 2);
     pdl = pdl && st->use_pdl;
     switch (m.ell_w) {
         case 7:
-            launch_k(pdl, k_sweep32<kFinal, 7>, grid, block, s, m, st->phys, b, cur, prv, a, c, first, have_x64);
+            launch_sweep_w<kFinal, 7>(st, m, b, s, cur, prv, a, c, first, have_x64, pdl);
             break;
         case 9:
-            launch_k(pdl, k_sweep32<kFinal, 9>, grid, block, s, m, st->phys, b, cur, prv, a, c, first, have_x64);
+            launch_sweep_w<kFinal, 9>(st, m, b, s, cur, prv, a, c, first, have_x64, pdl);
             break;
         case 12:
-            launch_k(pdl, k_sweep32<kFinal, 12>, grid, block, s, m, st->phys, b, cur, prv, a, c, first, have_x64);
+            launch_sweep_w<kFinal, 12>(st, m, b, s, cur, prv, a, c, first, have_x64, pdl);
             break;
         case 16:
-            launch_k(pdl, k_sweep32<kFinal, 16>, grid, block, s, m, st->phys, b, cur, prv, a, c, first, have_x64);
+            launch_sweep_w<kFinal, 16>(st, m, b, s, cur, prv, a, c, first, have_x64, pdl);
             break;
         default:
             k_cheb32<kFinal><<<grid_for(m.N, 128), 128, 0, s>>>(m, st->phys, b, cur, prv, a, c, first, have_x64);
@@ -1940,30 +1970,24 @@ int felbm_batch_schedule(felbm_state* st, int32_t cta_max_nodes) {
 
 }  // extern "C"
 
-namespace felbm {
 
-// Copy the FP32-deviation state (dpsi, C, p, u) to or from the staging buffer.
-static int save_restore_dev32(felbm_state* st, bool save) {
-    const DevMesh& m = st->dm;
-    const Bufs& b = st->buf;
-    char* stage = reinterpret_cast<char*>(b.stage);
-    const size_t nf = 18 * (size_t)m.Np * sizeof(float), nd = (size_t)m.Np * sizeof(double),
-                 n1 = (size_t)m.Np * sizeof(float);
-    void* dev[5] = {b.dpsi, b.C, b.p32, b.ux32, b.uy32};
-    size_t len[5] = {nf, nd, n1, n1, n1};
-    size_t off = 0;
-    for (int k = 0; k < 5; ++k) {
-        void* dst = save ? (void*)(stage + off) : dev[k];
-        const void* src = save ? dev[k] : (const void*)(stage + off);
-        FELBM_CUDA(cudaMemcpyAsync(dst, src, len[k], cudaMemcpyDeviceToDevice, st->stream));
-        off += (len[k] + 255) & ~size_t(255);
-    }
-    return FELBM_OK;
-}
-
-}  // namespace felbm
 
 extern "C" {
+
+static int checkpoint_copy(felbm_state* st, void* dst_v, const void* src_v, bool save);
+
+// Mean device time of one step over `trials` steps after one warm-up step.
+static int time_steps(felbm_state* st, int32_t trials, cudaEvent_t e0, cudaEvent_t e1, float* ms) {
+    int rc = felbm_step(st, 1);
+    if (rc) return rc;
+    FELBM_CUDA(cudaEventRecord(e0, st->stream));
+    if ((rc = felbm_step(st, trials)) != FELBM_OK) return rc;
+    FELBM_CUDA(cudaEventRecord(e1, st->stream));
+    FELBM_CUDA(cudaEventSynchronize(e1));
+    FELBM_CUDA(cudaEventElapsedTime(ms, e0, e1));
+    *ms /= trials;
+    return FELBM_OK;
+}
 
 int felbm_autotune(felbm_state* st, int32_t trials, felbm_tune_result* out) {
     if (!st || !out || trials < 1) {
@@ -1972,13 +1996,9 @@ int felbm_autotune(felbm_state* st, int32_t trials, felbm_tune_result* out) {
     }
     *out = felbm_tune_result{};
     const HostMesh& h = st->hm;
-    if (!st->dev32 || h.G < 2) {
-        out->cta_max_nodes = 0;
-        out->n_candidates = 0;
-        return felbm_batch_schedule(st, 0);
-    }
     FELBM_CUDA(cudaStreamSynchronize(st->stream));
-    int rc = save_restore_dev32(st, true);
+    void* save = st->buf.stage;   // the state fits the staging buffer in both precisions
+    int rc = checkpoint_copy(st, save, nullptr, true);
     if (rc) return rc;
     const int64_t step0 = st->step;
     const bool timing0 = st->timing;
@@ -1986,38 +2006,57 @@ int felbm_autotune(felbm_state* st, int32_t trials, felbm_tune_result* out) {
     cudaEvent_t e0, e1;
     FELBM_CUDA(cudaEventCreate(&e0));
     FELBM_CUDA(cudaEventCreate(&e1));
-    std::vector<int32_t> cand = {0, 1 << 11, 1 << 12, 1 << 13, 1 << 14, 1 << 15, 1 << 16, 1 << 17};
-    int last_n_cta = -1;
+    // 1. threads per node of the FP32 sweeps (tiled schedule)
+    const int parts_c[4] = {1, 2, 3, 6};
+    int best_parts = st->sweep_parts;
     float best = 1e30f;
+    if (st->mode != FELBM_SOLVER_FP64 && st->dm.ell_w > 0) {
+        rc = set_schedule(st, 0);
+        for (int k = 0; k < 4 && rc == FELBM_OK; ++k) {
+            st->sweep_parts = parts_c[k];
+            drop_graph(st);
+            float ms = 0.0f;
+            if ((rc = time_steps(st, trials, e0, e1, &ms)) != FELBM_OK) break;
+            out->parts_ms[k] = ms;
+            if (ms < best) {
+                best = ms;
+                best_parts = parts_c[k];
+            }
+            rc = checkpoint_copy(st, nullptr, save, false);
+        }
+    }
+    st->sweep_parts = best_parts;
+    out->sweep_parts = best_parts;
+    // 2. batch schedule: CTA per member up to a node threshold (FP32_DEV batches)
     int32_t best_t = 0;
-    for (int32_t t : cand) {
-        int32_t n_cta = 0;
-        for (int32_t g = 0; g < h.G; ++g) n_cta += (t > 0 && h.grp_size[g] <= t);
-        if (n_cta == last_n_cta) continue;   // same split as the previous candidate
-        last_n_cta = n_cta;
-        if ((rc = felbm_batch_schedule(st, t)) != FELBM_OK) break;
-        if ((rc = felbm_step(st, 1)) != FELBM_OK) break;
-        FELBM_CUDA(cudaEventRecord(e0, st->stream));
-        if ((rc = felbm_step(st, trials)) != FELBM_OK) break;
-        FELBM_CUDA(cudaEventRecord(e1, st->stream));
-        FELBM_CUDA(cudaEventSynchronize(e1));
-        float ms = 0.0f;
-        FELBM_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-        ms /= trials;
-        if (out->n_candidates < 16) {
-            out->candidates[out->n_candidates] = t;
-            out->step_ms[out->n_candidates] = ms;
-            out->n_candidates++;
+    if (rc == FELBM_OK && st->dev32 && h.G > 1) {
+        std::vector<int32_t> cand = {0, 1 << 11, 1 << 12, 1 << 13, 1 << 14, 1 << 15, 1 << 16, 1 << 17};
+        int last_n_cta = -1;
+        best = 1e30f;
+        for (int32_t t : cand) {
+            int32_t n_cta = 0;
+            for (int32_t g = 0; g < h.G; ++g) n_cta += (t > 0 && h.grp_size[g] <= t);
+            if (n_cta == last_n_cta) continue;   // same split as the previous candidate
+            last_n_cta = n_cta;
+            if ((rc = set_schedule(st, t)) != FELBM_OK) break;
+            drop_graph(st);
+            float ms = 0.0f;
+            if ((rc = time_steps(st, trials, e0, e1, &ms)) != FELBM_OK) break;
+            if (out->n_candidates < 16) {
+                out->candidates[out->n_candidates] = t;
+                out->step_ms[out->n_candidates] = ms;
+                out->n_candidates++;
+            }
+            if (ms < best) {
+                best = ms;
+                best_t = t;
+            }
+            if ((rc = checkpoint_copy(st, nullptr, save, false)) != FELBM_OK) break;
         }
-        if (ms < best) {
-            best = ms;
-            best_t = t;
-        }
-        if ((rc = save_restore_dev32(st, false)) != FELBM_OK) break;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    int rc2 = save_restore_dev32(st, false);
+    int rc2 = checkpoint_copy(st, nullptr, save, false);
     FELBM_CUDA(cudaStreamSynchronize(st->stream));
     st->step = step0;
     st->timing = timing0;

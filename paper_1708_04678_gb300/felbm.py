@@ -84,12 +84,15 @@ class StepTiming(ctypes.Structure):
 
 
 class TuneResult(ctypes.Structure):
-    _fields_ = [("cta_max_nodes", ctypes.c_int32), ("n_candidates", ctypes.c_int32),
+    _fields_ = [("sweep_parts", ctypes.c_int32), ("parts_ms", ctypes.c_float * 4),
+                ("cta_max_nodes", ctypes.c_int32), ("n_candidates", ctypes.c_int32),
                 ("candidates", ctypes.c_int32 * 16), ("step_ms", ctypes.c_float * 16)]
 
     def as_dict(self):
         n = self.n_candidates
-        return {"cta_max_nodes": self.cta_max_nodes,
+        return {"sweep_parts": self.sweep_parts,
+                "parts_ms": dict(zip((1, 2, 3, 6), [round(x, 5) for x in self.parts_ms])),
+                "cta_max_nodes": self.cta_max_nodes,
                 "candidates": list(self.candidates[:n]), "step_ms": list(self.step_ms[:n])}
 
 
