@@ -55,6 +55,15 @@ def workload():
     return I.free_droplet_256()
 
 
+def workload_config(w, world=1):
+    """The `config` object of both arms: what the workload is."""
+    return {"workload": "free droplet 256x256: 131,585 grid points (131,072 nodes), 4 triangles per cell, "
+                        "jitter 0.25h, density ratio 100, R 48, dt 0.05",
+            "nodes": len(w["mesh"]["xy"]), "triangles": len(w["mesh"]["tri"]), "dt": w["phys"]["dt"],
+            "l2": "flushed before every timed step (256 MiB write)",
+            "parallelism": f"replicas x{world}"}
+
+
 # ------------------------------------------------------------- CPU oracle --
 def run_oracle(budget_s, max_steps, warmup):
     """Time the FP64 oracle on full-size steps of the workload; returns
@@ -132,6 +141,35 @@ class ClockSampler:
                           for k in range(4) if r[5 + k].lower() == "active"})
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(self.rows)}
+
+
+def source_hash():
+    """sha256 of the CUDA library's sources (to tell whether a recorded ncu
+    figure still describes the kernels that run)."""
+    import hashlib
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1708_04678_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(f.read())
+    with open(os.path.join(ROOT, "include", "felbm.h"), "rb") as f:
+        h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel):
+    """DRAM bytes per launch of `kernel` from profiles/roofline_traffic.txt
+    (lines: kernel, source hash, bytes), if recorded for these sources."""
+    path = os.path.join(ROOT, "profiles", "roofline_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    h = source_hash()
+    with open(path) as f:
+        for line in f:
+            parts = line.split()
+            if len(parts) >= 3 and not line.startswith("#") and parts[0] == kernel and parts[1] == h:
+                return float(parts[2])
+    return None
 
 
 def peaks():
@@ -335,18 +373,15 @@ def run_gpu(args):
             "vs_baseline": None,
             "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": "free droplet 256x256: 131,585 grid points (131,072 nodes), 4 tri/cell, "
-                                   "jitter 0.25h, rho ratio 100, FP32 deviation storage",
-                       "nodes": N, "triangles": r32["info"]["n_tri"], "dt": w["phys"]["dt"],
-                       "solver": f"FP32 Chebyshev, {r32['solve_launches'] + 1} sweeps",
-                       "l2": "flushed before every timed step (256 MiB write)",
-                       "parallelism": f"replicas x{world}"},
+            "config": dict(workload_config(w, world), precision="FP32 deviation storage (fp32_dev); "
+                           "plain FP64 in fp64", solver=f"FP32 Chebyshev, {r32['solve_launches'] + 1} sweeps"),
             "fp32_dev": s32,
             "fp64": s64,
             "batched": rb,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                         "frac": achieved / hbm_peak, "traffic": None,
-                         "kernel": "k_cheb32 (one FP32 Chebyshev sweep of the 18-RHS mass solve)",
+                         "frac": achieved / hbm_peak, "traffic": recorded_traffic("k_sweep32"),
+                         "kernel": "k_sweep32 (one FP32 Chebyshev sweep of the 18-RHS mass solve)",
+                         "source_hash": source_hash(),
                          "alg_bytes_per_launch": alg_bytes, "launch_ms": sweep_ms,
                          "peak_source": peak_src},
             "e2e": {"value": s32["e2e_value"], "unit": "node-updates/s",
@@ -363,16 +398,19 @@ def run_gpu(args):
 
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
     if rank != 0:
         return
     budget = 120.0
-    v, n, secs = run_oracle(budget, args.steps, min(args.warmup, 1))
-    sample = (f"{n} full-size steps (after {min(args.warmup, 1)} warm-up) of the 131,072-node free droplet, "
-              f"{secs:.1f} s, stopped at the step that passed {budget:.0f} s")
-    out = {"metric": METRIC, "value": v, "unit": "node-updates/s", "n_gpus": 0, "steps": n,
-           "warmup": min(args.warmup, 1), "ms_per_step": secs * 1e3 / n, "higher_is_better": True,
+    warm = min(args.warmup, 1)
+    v, n, secs = run_oracle(budget, args.steps, warm)
+    why = "the requested steps" if n >= args.steps else f"the first step past {budget:.0f} s"
+    sample = (f"{n} full-size steps (after {warm} warm-up) of the 131,072-node free droplet in {secs:.1f} s "
+              f"(stopped after {why}); FP64 numpy/scipy oracle, one host core")
+    out = {"metric": METRIC, "value": v, "unit": "node-updates/s", "n_gpus": world, "steps": n,
+           "warmup": warm, "ms_per_step": secs * 1e3 / n, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": "free droplet 256x256, 131,585 grid points, 4 tri/cell, jitter 0.25h, FP64"},
+           "config": workload_config(workload(), world),
            "impl": "reference",
            "cpu_baseline": {"value": v, "unit": "node-updates/s", "cores": 1, "kind": "oracle",
                             "sample": sample},

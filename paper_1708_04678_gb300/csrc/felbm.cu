@@ -1514,15 +1514,17 @@ int felbm_init(const felbm_mesh* mesh, const felbm_params* params, const double*
         return rc;
     }
     st->mass0 = dg.mass;
-    std::vector<felbm_diag> gd(std::max<int32_t>(h.G, 1));
-    rc = felbm_diagnostics_groups(st, nullptr, h.G, gd.data());
-    if (rc != FELBM_OK && rc != FELBM_ERR_NONFINITE) {
-        *out = nullptr;
-        delete st;
-        return rc;
+    st->gmass0.assign(h.G, dg.mass);
+    if (h.G > 1) {   // one member: its mass is the mass
+        std::vector<felbm_diag> gd(h.G);
+        rc = felbm_diagnostics_groups(st, nullptr, h.G, gd.data());
+        if (rc != FELBM_OK && rc != FELBM_ERR_NONFINITE) {
+            *out = nullptr;
+            delete st;
+            return rc;
+        }
+        for (int32_t g = 0; g < h.G; ++g) st->gmass0[g] = gd[g].mass;
     }
-    st->gmass0.resize(h.G);
-    for (int32_t g = 0; g < h.G; ++g) st->gmass0[g] = gd[g].mass;
     rc = set_schedule(st, 0);
     if (rc != FELBM_OK) {
         *out = nullptr;

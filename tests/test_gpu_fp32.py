@@ -128,3 +128,17 @@ def test_autotuned_sweep_split_gives_identical_steps():
     gb, hb = b.get_state()
     np.testing.assert_array_equal(ga, gb)
     np.testing.assert_array_equal(ha, hb)
+
+
+def test_free_droplet_256_fp32_full_size_against_oracle():
+    """The benchmark's workload and launch configuration (autotuned sweep
+    split) for three steps against the FP64 oracle, at FP32 level."""
+    w = I.free_droplet_256()
+    osim = oracle_sim(w)
+    gst = _dev(w)
+    gst.autotune(trials=2)
+    osim.step(3)
+    gst.step(3)
+    err = compare_states(osim, gst)
+    assert err["C"] < 1e-6, err
+    assert err["h"] < 1e-5 and err["g"] < 1e-3, err

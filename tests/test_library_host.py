@@ -87,3 +87,16 @@ def test_periodic_mesh_min_image(lib):
     assert info["n_nodes"] == 512 and info["n_wall_edges"] == 0
     assert abs(info["total_area"] - 256.0) < 1e-9
     assert abs(info["min_area"] - m["min_area"]) < 1e-12
+
+
+def test_empty_and_invalid_sizes_are_rejected(lib):
+    xy = np.array([[0.0, 0.0], [1.0, 0.0], [1.0, 1.0]])
+    with pytest.raises(F.FelbmError) as e:
+        F.Mesh(xy, np.zeros((0, 3), np.int32))
+    assert e.value.code == -1
+    with pytest.raises(F.FelbmError) as e:
+        F.Mesh(np.zeros((0, 2)), np.zeros((0, 3), np.int32))
+    assert e.value.code == -1
+    with pytest.raises(F.FelbmError) as e:                       # wall id beyond the table
+        F.Mesh(xy, [[0, 1, 2]], [[0, 1], [1, 2], [2, 0]], [0, 0, F.MAX_WALL_IDS])
+    assert e.value.code == -1
