@@ -42,7 +42,6 @@ __all__ = [
     "small_sessile",
     "small_free_droplet",
     "batch",
-    "capillary_channel",
 ]
 
 
@@ -299,77 +298,6 @@ def batch(workloads):
     phys["theta_deg"] = tuple(thetas)
     return {"name": f"batch of {len(workloads)} droplets", "meshes": meshes, "C0": np.concatenate(C0),
             "phys": phys, "members": members, "steps": max(w["steps"] for w in workloads)}
-
-
-def capillary_channel(H=16, L=128, reservoir=64, slab=8, theta=60.0, fill=16.0, jitter=0.1, seed=6,
-                      steps=20000):
-    """2D capillary intrusion (the channel analogue of the paper's capillary
-    tube, Sec. III.C).  A box periodic in x with neutral (90 degree) walls at
-    y = 0 and y = H + 2 slab holds two solid slabs of length L and thickness
-    ``slab`` that leave a channel of width H between them; the slab surfaces
-    are wetting walls (id 0, contact angle ``theta``), the box walls id 1.
-    Liquid fills the left reservoir and the first ``fill`` lattice units of
-    the channel; vapour the rest.  2-triangle cells, unit spacing; nodes not
-    on a wall are jittered by U(+-jitter)."""
-    nx = 2 * reservoir + L
-    ny = H + 2 * slab
-    x0, x1 = reservoir, reservoir + L                 # channel entrance and exit
-    ylo, yhi = slab, slab + H                          # channel walls
-    ncol, nrow = nx, ny + 1
-
-    def nid(ii, jj):
-        return jj * ncol + (ii % ncol)
-
-    def solid_cell(ci, cj):                            # cell (ci, cj) lies inside a slab
-        return x0 <= ci < x1 and (cj < ylo or cj >= yhi)
-
-    tris, used = [], np.zeros(ncol * nrow, dtype=bool)
-    for cj in range(ny):
-        for ci in range(nx):
-            if solid_cell(ci, cj):
-                continue
-            n00, n10, n11, n01 = nid(ci, cj), nid(ci + 1, cj), nid(ci + 1, cj + 1), nid(ci, cj + 1)
-            tris.append((n00, n10, n11))
-            tris.append((n00, n11, n01))
-    tri = np.asarray(tris, dtype=np.int64)
-    used[tri.reshape(-1)] = True
-    # boundary edges: used by one triangle
-    from collections import Counter
-    cnt = Counter()
-    for a, b, c in tri:
-        for e in ((a, b), (b, c), (c, a)):
-            cnt[(min(e), max(e))] += 1
-    wall_edges, wall_id = [], []
-    for (a, b), k in sorted(cnt.items()):
-        if k == 1:
-            ja, jb = a // ncol, b // ncol
-            outer = (ja == jb) and (ja == 0 or ja == ny)
-            wall_edges.append((a, b))
-            wall_id.append(1 if outer else 0)
-    wall_nodes = np.zeros(ncol * nrow, dtype=bool)
-    wall_nodes[np.asarray(wall_edges).reshape(-1)] = True
-    # compact node numbering
-    old = np.nonzero(used)[0]
-    new_of = -np.ones(ncol * nrow, dtype=np.int64)
-    new_of[old] = np.arange(len(old))
-    i, j = old % ncol, old // ncol
-    xy = np.stack([i.astype(np.float64), j.astype(np.float64)], axis=1)
-    rng = np.random.default_rng(seed)
-    jit = rng.uniform(-jitter, jitter, size=(len(old), 2))
-    jit[wall_nodes[old]] = 0.0
-    xy = xy + jit
-    mesh = {"xy": xy, "tri": new_of[tri].astype(np.int32),
-            "wall_edges": new_of[np.asarray(wall_edges)].astype(np.int32),
-            "wall_id": np.asarray(wall_id, dtype=np.int32), "period": (float(nx), 0.0),
-            "n_grid_points": len(old), "min_area": None}
-    mesh["min_area"] = float(_triangle_areas(mesh["xy"], mesh["tri"], mesh["period"]).min())
-    phys = _phys(theta_deg=(theta, 90.0))
-    xi = phys["xi"]
-    # liquid in [2, x0 + fill] (the left reservoir and the channel entrance)
-    xf = x0 + fill
-    C0 = (0.5 + 0.5 * np.tanh(2.0 * (xf - xy[:, 0]) / xi)) * (0.5 + 0.5 * np.tanh(2.0 * (xy[:, 0] - 2.0) / xi))
-    return {"name": f"capillary channel H={H} L={L}, {theta:.0f} deg", "mesh": mesh, "C0": C0, "phys": phys,
-            "steps": steps, "channel": (x0, x1, ylo, yhi), "fill": fill}
 
 
 def rough_wall_droplet(seed=4, width=2048, height=1024, rows=1017, R=300.0,
