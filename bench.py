@@ -29,6 +29,8 @@ import sys
 import threading
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
@@ -299,6 +301,73 @@ def time_batch(F, torch, dev, K, flush, barrier, world, dist):
             "max_abs_mass_drift_rel": max(abs(d["mass_drift_rel"]) for d in dg)}
 
 
+def time_adjoint(F, torch, dev, K):
+    """The FP64 forward step and its adjoint on the 128x64 sessile droplet
+    (8,320 nodes): device time per step of each."""
+    from paper_1708_04678_gb300 import inputs as I
+    w = I.sessile_droplet_128x64()
+    mesh = F.Mesh.from_dict(w["mesh"])
+    stream = torch.cuda.Stream(dev)
+    st = F.State(mesh, F.params_derive(w["phys"]), w["C0"], device=dev, stream=stream)
+    st.step(5)
+    g, h = st.get_state()
+    st.adjoint_seed(np.zeros_like(g), np.ones_like(h))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stream.synchronize()
+    e0.record(stream)
+    st.step(K)
+    e1.record(stream)
+    e1.synchronize()
+    fwd_ms = e0.elapsed_time(e1) / K
+    e0.record(stream)
+    for _ in range(K):
+        st.adjoint_step()
+    e1.record(stream)
+    e1.synchronize()
+    adj_ms = e0.elapsed_time(e1) / K
+    n = len(w["mesh"]["xy"])
+    st.close()
+    return {"workload": "sessile droplet 128x64 (8,320 nodes), FP64", "steps": K,
+            "forward_ms_per_step": fwd_ms, "adjoint_ms_per_step": adj_ms,
+            "adjoint_node_updates_per_s": n / (adj_ms * 1e-3), "adjoint_over_forward": adj_ms / fwd_ms}
+
+
+def time_large(F, torch, dev, K, flush):
+    """FP32-deviation steps of the 2048x1024 rough-wall droplet (2,082,816
+    nodes; state and solve working set far above L2): time per step and the
+    solve sweep's algorithmic bandwidth."""
+    from paper_1708_04678_gb300 import inputs as I
+    w = I.rough_wall_droplet()
+    mesh = F.Mesh.from_dict(w["mesh"])
+    stream = torch.cuda.Stream(dev)
+    st = F.State(mesh, F.params_derive(w["phys"], precision=F.FP32_DEV), w["C0"], device=dev, stream=stream)
+    st.timing_enable(True)
+    tune = st.autotune(trials=2)
+    for k in range(2):
+        st.step(1)
+    tot, phases = 0.0, []
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for k in range(K):
+        with torch.cuda.stream(stream):
+            flush.fill_(k & 255)
+        e0.record(stream)
+        st.step(1)
+        e1.record(stream)
+        phases.append(st.timing_get())
+        tot += e0.elapsed_time(e1)
+    n = len(w["mesh"]["xy"])
+    info = mesh.info()
+    solve = statistics.mean(p["solve_ms"] for p in phases)
+    sweep_ms = solve / phases[0]["solve_launches"]
+    alg = n * 4 * 18 * 4 + info["nnz"] * (4 + 4) + n * (4 + 4)   # as for the main roofline line
+    d = st.diagnostics(w["centre"], w["R"], 4.0, 0)
+    st.close()
+    return {"workload": "rough-wall droplet 2048x1024 (2,082,816 nodes), FP32 deviation storage",
+            "steps": K, "ms_per_step": tot / K, "value": n * K / (tot * 1e-3), "unit": "node-updates/s",
+            "sweep_ms": sweep_ms, "sweep_alg_GBps": alg / (sweep_ms * 1e-3) / 1e9, "autotune": tune,
+            "finite": d["status"] == 0}
+
+
 def run_gpu(args):
     import torch
     import torch.distributed as dist
@@ -335,6 +404,8 @@ def run_gpu(args):
         r32 = time_precision(F, torch, w, dev, F.FP32_DEV, K, W, flush, barrier, world, dist)
         r64 = time_precision(F, torch, w, dev, F.FP64, K, W, flush, barrier, world, dist)
         rb = None if args.no_batch else time_batch(F, torch, dev, max(3, K // 5), flush, barrier, world, dist)
+        radj = None if args.no_batch else time_adjoint(F, torch, dev, max(5, K // 2))
+        rl = None if args.no_batch else time_large(F, torch, dev, max(3, K // 10), flush)
 
     for name, r in (("FP32", r32), ("FP64", r64)):
         if r["diag"]["status"] != 0:
@@ -378,6 +449,8 @@ def run_gpu(args):
             "fp32_dev": s32,
             "fp64": s64,
             "batched": rb,
+            "adjoint": radj,
+            "large_mesh": rl,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                          "frac": achieved / hbm_peak, "traffic": recorded_traffic("k_sweep32"),
                          "kernel": "k_sweep32 (one FP32 Chebyshev sweep of the 18-RHS mass solve)",
