@@ -145,27 +145,32 @@ class ClockSampler:
                 "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(self.rows)}
 
 
-def source_hash():
-    """sha256 of the CUDA library's sources (to tell whether a recorded ncu
-    figure still describes the kernels that run)."""
+SOURCES_2D = ("felbm.cu", "felbm_dev32.cuh", "felbm_adjoint.cuh", "felbm_internal.h", "mesh.cpp", "felbm.h")
+SOURCES_3D = ("felbm3d.cu", "felbm3d_dev32.cuh", "felbm3d_internal.h", "mesh3d.cpp", "felbm_internal.h",
+              "felbm3d.h", "felbm.h")
+
+
+def source_hash(files=SOURCES_2D):
+    """sha256 prefix of the CUDA library sources a kernel is built from (to
+    tell whether a recorded ncu figure still describes the kernel that runs)."""
     import hashlib
     h = hashlib.sha256()
-    csrc = os.path.join(ROOT, "paper_1708_04678_gb300", "csrc")
-    for name in sorted(os.listdir(csrc)):
-        with open(os.path.join(csrc, name), "rb") as f:
-            h.update(f.read())
-    with open(os.path.join(ROOT, "include", "felbm.h"), "rb") as f:
-        h.update(f.read())
+    for name in files:
+        for d in (os.path.join(ROOT, "paper_1708_04678_gb300", "csrc"), os.path.join(ROOT, "include")):
+            path = os.path.join(d, name)
+            if os.path.exists(path):
+                with open(path, "rb") as f:
+                    h.update(f.read())
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(kernel):
+def recorded_traffic(kernel, files=SOURCES_2D):
     """DRAM bytes per launch of `kernel` from profiles/roofline_traffic.txt
     (lines: kernel, source hash, bytes), if recorded for these sources."""
     path = os.path.join(ROOT, "profiles", "roofline_traffic.txt")
     if not os.path.exists(path):
         return None
-    h = source_hash()
+    h = source_hash(files)
     with open(path) as f:
         for line in f:
             parts = line.split()

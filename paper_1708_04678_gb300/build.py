@@ -21,7 +21,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIBDIR = os.path.join(PKG, "lib")
 LIBNAME = "libfelbm.so"
-SOURCES = ["mesh.cpp", "felbm.cu"]
+SOURCES = ["mesh.cpp", "felbm.cu", "mesh3d.cpp", "felbm3d.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O3"]
 
@@ -39,11 +39,12 @@ def lib_path():
 
 def _stamp():
     h = hashlib.sha256()
-    for name in SOURCES + ["felbm_internal.h"]:
-        with open(os.path.join(CSRC, name), "rb") as f:
-            h.update(f.read())
-    with open(os.path.join(INCLUDE, "felbm.h"), "rb") as f:
-        h.update(f.read())
+    for d in (CSRC, INCLUDE):
+        for name in sorted(os.listdir(d)):
+            if name.endswith((".cu", ".cpp", ".h", ".cuh")):
+                with open(os.path.join(d, name), "rb") as f:
+                    h.update(name.encode())
+                    h.update(f.read())
     h.update(" ".join(ARCH + FLAGS).encode())
     h.update(platform.machine().encode())
     return h.hexdigest()

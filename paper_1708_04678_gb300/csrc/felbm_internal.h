@@ -11,6 +11,11 @@ namespace felbm {
 
 void set_error(const std::string& msg);
 
+// Reverse Cuthill-McKee order of a node graph given as CSR adjacency
+// (no self loops); returns order[new] = old.  Components one after another.
+std::vector<int32_t> rcm_order(int32_t N, const std::vector<int32_t>& adj_ptr,
+                               const std::vector<int32_t>& adj);
+
 // Host mesh after preprocessing.  Node ids are the internal (reverse
 // Cuthill-McKee) ids; perm[new] = caller id, iperm[caller] = new.
 struct HostMesh {

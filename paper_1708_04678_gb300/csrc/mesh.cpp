@@ -30,7 +30,7 @@ static double min_image(double d, double L) {
 }
 
 // Reverse Cuthill-McKee order of the node graph; returns order[new] = old.
-static std::vector<int32_t> rcm_order(int32_t N, const std::vector<int32_t>& adj_ptr,
+std::vector<int32_t> rcm_order(int32_t N, const std::vector<int32_t>& adj_ptr,
                                       const std::vector<int32_t>& adj) {
     std::vector<int32_t> order;
     order.reserve(N);

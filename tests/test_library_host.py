@@ -13,7 +13,7 @@ from paper_1708_04678_gb300 import build as B
 from paper_1708_04678_gb300 import felbm as F
 from paper_1708_04678_gb300 import inputs as I
 
-HEADER = os.path.join(B.INCLUDE, "felbm.h")
+HEADERS = [os.path.join(B.INCLUDE, n) for n in sorted(os.listdir(B.INCLUDE)) if n.endswith(".h")]
 
 
 @pytest.fixture(scope="module")
@@ -23,14 +23,17 @@ def lib():
 
 
 def _declared_functions():
-    src = open(HEADER).read()
-    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(felbm_[a-z_0-9]+)\s*\(", src)))
+    names = set()
+    for path in HEADERS:
+        src = re.sub(r"/\*.*?\*/", "", open(path).read(), flags=re.S)
+        names |= set(re.findall(r"\b(felbm(?:3d)?_[a-z_0-9]+)\s*\(", src))
+    return sorted(names)
 
 
 def test_header_symbols_are_exported(lib):
     names = _declared_functions()
     assert "felbm_step" in names and "felbm_mesh_create" in names
+    assert "felbm3d_step" in names and "felbm3d_mesh_create" in names
     for name in names:
         assert hasattr(lib, name), name
 
@@ -99,4 +102,44 @@ def test_empty_and_invalid_sizes_are_rejected(lib):
     assert e.value.code == -1
     with pytest.raises(F.FelbmError) as e:                       # wall id beyond the table
         F.Mesh(xy, [[0, 1, 2]], [[0, 1], [1, 2], [2, 0]], [0, 0, F.MAX_WALL_IDS])
+    assert e.value.code == -1
+
+
+# ------------------------------------------------------------ 3D meshes ---
+def test_mesh3d_tables(lib):
+    from paper_1708_04678_gb300 import felbm3d as F3
+    from paper_1708_04678_gb300 import inputs3d as I3
+    w = I3.small_sessile_3d(n=10, nz=6)
+    mesh = F3.Mesh3D.from_dict(w["mesh"])
+    info = mesh.info()
+    assert info["n_nodes"] == 10 * 10 * 7 and info["n_tet"] == 6 * 10 * 10 * 6
+    assert info["n_wall_faces"] == 2 * 2 * 10 * 10
+    assert info["max_degree"] == 15 and info["max_incidence"] == 24   # Kuhn: 14 neighbours, 24 tetrahedra
+    assert info["nnz"] == 15 * 10 * 10 * 5 + 11 * 2 * 10 * 10        # wall rows: 10 neighbours
+    assert abs(info["total_volume"] - 600.0) < 1e-9
+    p = F.params_derive(w["phys"])
+    assert mesh.workspace_bytes(p) > 38 * 8 * info["n_nodes"]
+    periodic = F3.Mesh3D.from_dict(I3.kuhn_box(6, 5, 4, 0.15, 2, walls=False))
+    assert periodic.info()["nnz"] == 15 * 6 * 5 * 4 and periodic.info()["n_wall_faces"] == 0
+
+
+def test_mesh3d_validation(lib):
+    from paper_1708_04678_gb300 import felbm3d as F3
+    xyz = np.array([[0.0, 0.0, 0.0], [1.0, 0.0, 0.0], [0.0, 1.0, 0.0], [0.0, 0.0, 1.0]])
+    faces = [[0, 1, 2], [0, 1, 3], [0, 2, 3], [1, 2, 3]]
+    F3.Mesh3D(xyz, [[0, 1, 2, 3]], faces, [0, 0, 0, 0])                  # valid tetrahedron
+    with pytest.raises(F.FelbmError) as e:                                 # inverted
+        F3.Mesh3D(xyz, [[0, 2, 1, 3]], faces, [0, 0, 0, 0])
+    assert e.value.code == -2
+    with pytest.raises(F.FelbmError) as e:                                 # boundary face not a wall
+        F3.Mesh3D(xyz, [[0, 1, 2, 3]], faces[:3], [0, 0, 0])
+    assert e.value.code == -2
+    with pytest.raises(F.FelbmError) as e:                                 # node out of range
+        F3.Mesh3D(xyz, [[0, 1, 2, 9]], faces, [0, 0, 0, 0])
+    assert e.value.code == -1
+    with pytest.raises(F.FelbmError) as e:                                 # repeated node
+        F3.Mesh3D(xyz, [[0, 1, 1, 3]], faces, [0, 0, 0, 0])
+    assert e.value.code == -1
+    with pytest.raises(F.FelbmError) as e:                                 # wall id beyond the table
+        F3.Mesh3D(xyz, [[0, 1, 2, 3]], faces, [0, 0, 0, F.MAX_WALL_IDS])
     assert e.value.code == -1
