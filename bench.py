@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--only-3d", action="store_true",
+                    help="time only the 3D (D3Q19, tetrahedra) section and print it as one JSON line")
     return ap.parse_args()
 
 
@@ -373,6 +375,60 @@ def time_large(F, torch, dev, K, flush):
             "finite": d["status"] == 0}
 
 
+def time_3d(torch, dev, K, flush):
+    """The paper's own setting: D3Q19 on linear tetrahedra, the 64^3 static
+    droplet (262,144 nodes, 1,572,864 tetrahedra; state and solve working
+    set above L2).  FP32 deviation storage and FP64 (mixed solve): time per
+    step, phases, and the roofline of the FP32 solve sweep."""
+    from paper_1708_04678_gb300 import felbm as F
+    from paper_1708_04678_gb300 import felbm3d as F3
+    from paper_1708_04678_gb300 import inputs3d as I3
+    w = I3.static_droplet_64()
+    mesh = F3.Mesh3D.from_dict(w["mesh"])
+    info = mesh.info()
+    n = info["n_nodes"]
+    out = {"workload": "static droplet 64^3 (262,144 nodes, 1,572,864 tetrahedra), D3Q19, R=16, xi=4, "
+                       "density ratio 2", "nodes": n}
+    for name, prec in (("fp32_dev", F.FP32_DEV), ("fp64", F.FP64)):
+        stream = torch.cuda.Stream(dev)
+        st = F3.State3D(mesh, F.params_derive(w["phys"], precision=prec), w["C0"], device=dev, stream=stream)
+        st.timing_enable(True)
+        for k in range(3):
+            st.step(1)
+        tot, phases = 0.0, []
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        for k in range(K):
+            with torch.cuda.stream(stream):
+                flush.fill_(k & 255)
+            e0.record(stream)
+            st.step(1)
+            e1.record(stream)
+            phases.append(st.timing_get())
+            tot += e0.elapsed_time(e1)
+        d = st.diagnostics(w["centre"], w["R"], w["phys"]["xi"], substrate=-1)
+        ph = {k: statistics.mean(p[k] for p in phases) for k in phases[0]}
+        r = {"ms_per_step": tot / K, "value": n * K / (tot * 1e-3), "unit": "node-updates/s",
+             "phase_ms": {k: round(v, 5) for k, v in ph.items()}, "launches_per_step": st.launches(),
+             "after_timed_steps": {k: d[k] for k in ("max_u", "delta_p", "mass_drift_rel", "interface_rho_uu",
+                                                     "status")}}
+        if prec == F.FP32_DEV:
+            sweeps = st.launches() - 4                       # mu, grad mu, element, rhs + the solve
+            sweep_ms = ph["solve_ms"] / sweeps
+            # one sweep: gathered x_k, own x_{k-1}, rhs, new x (4 x 38 floats per
+            # node), the mass row (column + FP32 value per entry), 1/m_i per node
+            alg = n * (4 * 38 * 4 + 4) + info["nnz"] * (4 + 4)
+            hbm_peak, src = peaks()
+            ach = alg / (sweep_ms * 1e-3) / 1e9
+            r["roofline"] = {"bound": "hbm", "kernel": "k3_sweep32 (one FP32 Chebyshev sweep, 38 RHS)",
+                             "achieved": ach, "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak,
+                             "traffic": recorded_traffic("k3_sweep32", SOURCES_3D),
+                             "source_hash": source_hash(SOURCES_3D), "alg_bytes_per_launch": alg,
+                             "launch_ms": sweep_ms, "peak_source": src}
+        out[name] = r
+        st.close()
+    return out
+
+
 def run_gpu(args):
     import torch
     import torch.distributed as dist
@@ -411,6 +467,7 @@ def run_gpu(args):
         rb = None if args.no_batch else time_batch(F, torch, dev, max(3, K // 5), flush, barrier, world, dist)
         radj = None if args.no_batch else time_adjoint(F, torch, dev, max(5, K // 2))
         rl = None if args.no_batch else time_large(F, torch, dev, max(3, K // 10), flush)
+        r3 = None if args.no_batch else time_3d(torch, dev, max(5, K // 5), flush)
 
     for name, r in (("FP32", r32), ("FP64", r64)):
         if r["diag"]["status"] != 0:
@@ -456,6 +513,7 @@ def run_gpu(args):
             "batched": rb,
             "adjoint": radj,
             "large_mesh": rl,
+            "tetrahedra_3d": r3,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                          "frac": achieved / hbm_peak, "traffic": recorded_traffic("k_sweep32"),
                          "kernel": "k_sweep32 (one FP32 Chebyshev sweep of the 18-RHS mass solve)",
@@ -506,6 +564,16 @@ def main():
         return
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.only_3d:
+        import torch
+        from paper_1708_04678_gb300 import build as B
+        B.build()
+        dev = torch.device("cuda", 0)
+        flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+        with ClockSampler(0) as clk:
+            r3 = time_3d(torch, dev, args.steps, flush)
+        print(json.dumps({"tetrahedra_3d": r3, "clocks": clk.summary()}), flush=True)
         return
     run_gpu(args)
 

@@ -160,18 +160,18 @@ struct Bufs3 {
     double* rhs;     // [38][Np]
     double* x0;      // [38][Np] FP64 Chebyshev iterates; mixed solve: x64 and rho64
     double* x1;
-    float* r32;      // [38][Np] FP32 residual of the current correction
-    float* e0;       // [38][Np] FP32 Chebyshev iterates
+    float* r32;      // [Np][kRow] FP32 residual of the current correction
+    float* e0;       // [Np][kRow] FP32 Chebyshev iterates
     float* e1;
     // FP32-deviation storage (FELBM_FP32_DEV); C above stays FP64
-    float* dpsi;     // [38][Np]
+    float* dpsi;     // [Np][kRow] deviations from equilibrium
     float* p32;
     float* ux32;
     float* uy32;
     float* uz32;
     float* mu32;
     float* gmu32;    // [3][Tp]
-    float* R32;      // [T][40] (38 used, rows 16-byte aligned)
+    float* R32;      // [T][kRow]
     double* stage;   // [38][N] caller-order staging
     double* diag_part; // [kDiagBlocks][kDiagSlots]
     double* diag_out;  // [kDiagSlots]
@@ -181,7 +181,56 @@ constexpr int kBlock = 256;
 constexpr int kNodeBlock = 128;
 constexpr int kDiagBlocks = 304;   // fixed grid (2 x 152 SMs): the reduction order never changes
 constexpr int kDiagSlots = 12;
-constexpr int kR32 = 40;           // FP32 residual row length
+// FP32 rows (deviations, element residuals, solve iterates): 40 floats per
+// node or tetrahedron, g_q at 20*0 + q, h_q at 20*1 + q, slots 19 and 39
+// zero -- each set is five 16-byte vectors.
+constexpr int kRow = 40;
+__host__ __device__ constexpr int slot(int s, int q) { return 20 * s + q; }
+
+// Cooperative kernels: a group of kGroup = 5 lanes per node (or
+// tetrahedron); lane c owns directions 4c..4c+3 of both sets, i.e. the
+// 16-byte vectors c and 5 + c of a row, so one warp load reads whole rows
+// of six items contiguously.  Lanes 30 and 31 of each warp idle.
+constexpr int kGroup = 5;
+constexpr int kGroupsPerWarp = 6;
+constexpr int kCoopBlock = 128;
+constexpr int kItemsPerBlock = kGroupsPerWarp * (kCoopBlock / 32);
+
+struct Coop {
+    int lane, grp, c, item;
+    bool active;
+};
+__device__ __forceinline__ Coop coop_index(int n_items) {
+    Coop k;
+    k.lane = threadIdx.x & 31;
+    k.grp = k.lane / kGroup;
+    k.c = k.lane - k.grp * kGroup;
+    k.item = (blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * kGroupsPerWarp + k.grp;
+    k.active = k.grp < kGroupsPerWarp && k.item < n_items;
+    return k;
+}
+// sum of v over the lanes of this lane's group, in lane order (identical in
+// every lane of the group); every lane of the warp must call it
+__device__ __forceinline__ float group_sum(float v, const Coop& k) {
+    const int base = k.grp * kGroup;
+    float s = __shfl_sync(0xffffffffu, v, base);
+#pragma unroll
+    for (int l = 1; l < kGroup; ++l) s += __shfl_sync(0xffffffffu, v, base + l);
+    return s;
+}
+__device__ __forceinline__ void fma4(float4& acc, float w, const float4& x) {
+    acc.x = fmaf(w, x.x, acc.x);
+    acc.y = fmaf(w, x.y, acc.y);
+    acc.z = fmaf(w, x.z, acc.z);
+    acc.w = fmaf(w, x.w, acc.w);
+}
+__device__ __forceinline__ float comp(const float4& v, int j) { return j == 0 ? v.x : j == 1 ? v.y : j == 2 ? v.z : v.w; }
+__device__ __forceinline__ void set_comp(float4& v, int j, float x) {
+    if (j == 0) v.x = x;
+    else if (j == 1) v.y = x;
+    else if (j == 2) v.z = x;
+    else v.w = x;
+}
 
 // ------------------------------------------------------ K1: collision -----
 // Moments of the pre-collision state (C = sum h, p = sum g, rho u = sum e g /
@@ -407,11 +456,16 @@ __global__ void __launch_bounds__(kNodeBlock) k3_rhs(DevMesh3 m, Phys3 c, Bufs3 
         const size_t r = (size_t)(19 * s + q) * Np + i;
         b.rhs[r] = acc[q];
         if (kMixed) {
-            b.r32[r] = (float)acc[q];
-            b.e1[r] = (float)(acc[q] * sc);
+            const size_t a = (size_t)i * kRow + slot(s, q);
+            b.r32[a] = (float)acc[q];
+            b.e1[a] = (float)(acc[q] * sc);
         } else {
             b.x1[r] = acc[q] * sc;
         }
+    }
+    if (kMixed) {
+        b.r32[(size_t)i * kRow + slot(s, 19)] = 0.0f;
+        b.e1[(size_t)i * kRow + slot(s, 19)] = 0.0f;
     }
 }
 
@@ -468,79 +522,90 @@ __global__ void __launch_bounds__(kNodeBlock) k3_refine(DevMesh3 m, Bufs3 b, con
     double acc[19];
 #pragma unroll
     for (int q = 0; q < 19; ++q) acc[q] = 0.0;
+    const int s = blockIdx.y;
     for (int k = m.row_ptr[i]; k < m.row_ptr[i + 1]; ++k) {
-        const int j = m.col[k];
+        const float* ej = e + (size_t)m.col[k] * kRow + slot(s, 0);
         const double mv = m.mval[k];
 #pragma unroll
-        for (int q = 0; q < 19; ++q) acc[q] += mv * (double)e[off + (size_t)q * Np + j];
+        for (int q = 0; q < 19; ++q) acc[q] += mv * (double)ej[q];
     }
     const double sc = m.inv_lumped[i] * inv_theta;
+    const size_t a0 = (size_t)i * kRow + slot(s, 0);
 #pragma unroll
     for (int q = 0; q < 19; ++q) {
         const size_t r = off + (size_t)q * Np + i;
         double xo = first_round ? 0.0 : b.x0[r];
         double ro = first_round ? b.rhs[r] : b.x1[r];
         double rn = ro - acc[q];
-        b.x0[r] = xo + (double)e[r];
+        b.x0[r] = xo + (double)e[a0 + q];
         b.x1[r] = rn;
-        b.r32[r] = (float)rn;
-        next_first[r] = (float)(rn * sc);
+        b.r32[a0 + q] = (float)rn;
+        next_first[a0 + q] = (float)(rn * sc);
     }
 }
 
 // ------------------------------------------------ FP32 Chebyshev sweep ----
-// kSplit = 2: one thread per (node, set), 19 directions (grid.y = 2);
-// kSplit = 1: one thread per node, all 38 directions.  The matrix is read
-// from the column-major ELL copy (coalesced) when the mesh has one.
-__device__ void dev32_update3(const DevMesh3& m, const Phys3& c, const Bufs3& b, int i, const float* d);
+// One group of five lanes per node; the iterates and the residual are
+// node-major rows, the matrix is read from the column-major ELL copy
+// (coalesced) when the mesh has one.
+__device__ void dev32_update3(const DevMesh3& m, const Phys3& c, const Bufs3& b, const Coop& k, int i,
+                              const float4& dg, const float4& dh);
 
-template <int kFinal, int kSplit>
-__global__ void __launch_bounds__(kNodeBlock) k3_sweep32(DevMesh3 m, Phys3 c, Bufs3 b, const float* __restrict__ cur,
+template <int kFinal>
+__global__ void __launch_bounds__(kCoopBlock) k3_sweep32(DevMesh3 m, Phys3 c, Bufs3 b, const float* __restrict__ cur,
                                                          float* prev, float a, float cc, int first, int have_x64) {
-    constexpr int Q = 38 / kSplit;
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= m.N) return;
+    const Coop k = coop_index(m.N);
+    const int i = k.active ? k.item : 0;      // idle lanes read node 0 and write nothing
     const int Np = m.Np;
-    const size_t off = kSplit == 2 ? (size_t)19 * blockIdx.y * Np : 0;
-    const float* cu = cur + off;
-    float acc[Q];
-#pragma unroll
-    for (int q = 0; q < Q; ++q) acc[q] = 0.0f;
-    if (m.ell_w > 0) {
-        for (int k = 0; k < m.ell_w; ++k) {
-            const int j = m.ell_col[k * Np + i];
-            const float v = m.ell_val[k * Np + i];
-#pragma unroll
-            for (int q = 0; q < Q; ++q) acc[q] = fmaf(v, cu[q * Np + j], acc[q]);
-        }
-    } else {
-        for (int k = m.row_ptr[i]; k < m.row_ptr[i + 1]; ++k) {
-            const int j = m.col[k];
-            const float v = m.mval32[k];
-#pragma unroll
-            for (int q = 0; q < Q; ++q) acc[q] = fmaf(v, cu[q * Np + j], acc[q]);
+    float4 ag = make_float4(0.0f, 0.0f, 0.0f, 0.0f), ah = ag;
+    if (k.active) {
+        if (m.ell_w > 0) {
+            for (int e = 0; e < m.ell_w; ++e) {
+                const float4* row = reinterpret_cast<const float4*>(cur + (size_t)m.ell_col[e * Np + i] * kRow);
+                const float v = m.ell_val[e * Np + i];
+                fma4(ag, v, row[k.c]);
+                fma4(ah, v, row[5 + k.c]);
+            }
+        } else {
+            for (int e = m.row_ptr[i]; e < m.row_ptr[i + 1]; ++e) {
+                const float4* row = reinterpret_cast<const float4*>(cur + (size_t)m.col[e] * kRow);
+                const float v = m.mval32[e];
+                fma4(ag, v, row[k.c]);
+                fma4(ah, v, row[5 + k.c]);
+            }
         }
     }
     const float sc = cc * m.inv_lumped32[i];
-    float d[Q];
+    const size_t own = (size_t)i * kRow;
+    const float4* xk4 = reinterpret_cast<const float4*>(cur + own);
+    const float4* xm4 = reinterpret_cast<const float4*>(prev + own);
+    const float4* r4 = reinterpret_cast<const float4*>(b.r32 + own);
+    float4 xn[2];
 #pragma unroll
-    for (int q = 0; q < Q; ++q) {
-        const size_t r = off + (size_t)q * Np + i;
-        float xk = cur[r];
-        float xm = first ? 0.0f : prev[r];
-        float xn = xk + a * (xk - xm) + sc * (b.r32[r] - acc[q]);
-        if (kFinal == kStore3) {
-            prev[r] = xn;
-        } else if (kFinal == kAddPsi3) {
-            b.psi[r] += have_x64 ? b.x0[r] + (double)xn : (double)xn;
-        } else {
-            d[q] = xn;
+    for (int h = 0; h < 2; ++h) {
+        const int v = 5 * h + k.c;
+        const float4 xk = xk4[v], rr = r4[v], acc = h ? ah : ag;
+        const float4 xm = first ? make_float4(0.0f, 0.0f, 0.0f, 0.0f) : xm4[v];
+        xn[h].x = xk.x + a * (xk.x - xm.x) + sc * (rr.x - acc.x);
+        xn[h].y = xk.y + a * (xk.y - xm.y) + sc * (rr.y - acc.y);
+        xn[h].z = xk.z + a * (xk.z - xm.z) + sc * (rr.z - acc.z);
+        xn[h].w = xk.w + a * (xk.w - xm.w) + sc * (rr.w - acc.w);
+        if (kFinal == kStore3 && k.active) reinterpret_cast<float4*>(prev + own)[v] = xn[h];
+    }
+    if constexpr (kFinal == kAddPsi3) {
+        // FP64 storage: psi += x64 + e for this lane's directions
+        if (k.active) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int q = 4 * k.c + j;
+                if (q >= 19) continue;
+                const size_t rg = (size_t)q * Np + i, rh = (size_t)(19 + q) * Np + i;
+                b.psi[rg] += have_x64 ? b.x0[rg] + (double)comp(xn[0], j) : (double)comp(xn[0], j);
+                b.psi[rh] += have_x64 ? b.x0[rh] + (double)comp(xn[1], j) : (double)comp(xn[1], j);
+            }
         }
     }
-    if constexpr (kFinal == kUpdateDev3) {
-        static_assert(kFinal != kUpdateDev3 || kSplit == 1, "the deviation update needs all 38 increments");
-        dev32_update3(m, c, b, i, d);
-    }
+    if constexpr (kFinal == kUpdateDev3) dev32_update3(m, c, b, k, i, xn[0], xn[1]);
 }
 
 // ----------------------------------------------- permutation kernels ------
@@ -790,18 +855,18 @@ static size_t carve3(const HostMesh3D& h, bool dev32, void* base, DevMesh3* dm, 
         b.x0 = cv.take<double>(38 * Np);
         b.x1 = cv.take<double>(38 * Np);
     } else {
-        b.dpsi = cv.take<float>(38 * Np);
+        b.dpsi = cv.take<float>((size_t)kRow * Np);
         b.p32 = cv.take<float>(Np);
         b.ux32 = cv.take<float>(Np);
         b.uy32 = cv.take<float>(Np);
         b.uz32 = cv.take<float>(Np);
         b.mu32 = cv.take<float>(Np);
         b.gmu32 = cv.take<float>(3 * Tp);
-        b.R32 = cv.take<float>((size_t)kR32 * std::max<int32_t>(h.T, 1));
+        b.R32 = cv.take<float>((size_t)kRow * std::max<int32_t>(h.T, 1));
     }
-    b.r32 = cv.take<float>(38 * Np);
-    b.e0 = cv.take<float>(38 * Np);
-    b.e1 = cv.take<float>(38 * Np);
+    b.r32 = cv.take<float>((size_t)kRow * Np);
+    b.e0 = cv.take<float>((size_t)kRow * Np);
+    b.e1 = cv.take<float>((size_t)kRow * Np);
     b.stage = cv.take<double>(38 * (size_t)h.N);
     b.diag_part = cv.take<double>(kDiagBlocks * kDiagSlots);
     b.diag_out = cv.take<double>(kDiagSlots);
@@ -908,13 +973,13 @@ static void enqueue_solve3(felbm3d_state* st, cudaStream_t s) {
         for (int k = 1; k < st->sweeps; ++k) {
             const float a = (float)st->cheb_a[k], c = (float)st->cheb_c[k];
             const bool last = r == st->rounds - 1 && k == st->sweeps - 1;
+            const unsigned gc = grid_for(m.N, kItemsPerBlock);
             if (!last)
-                k3_sweep32<kStore3, 2><<<g2, kNodeBlock, 0, s>>>(m, st->phys, b, cur, prv, a, c, k == 1, have_x64);
+                k3_sweep32<kStore3><<<gc, kCoopBlock, 0, s>>>(m, st->phys, b, cur, prv, a, c, k == 1, have_x64);
             else if (st->dev32)
-                k3_sweep32<kUpdateDev3, 1><<<grid_for(m.N, kNodeBlock), kNodeBlock, 0, s>>>(m, st->phys, b, cur, prv, a,
-                                                                                           c, k == 1, have_x64);
+                k3_sweep32<kUpdateDev3><<<gc, kCoopBlock, 0, s>>>(m, st->phys, b, cur, prv, a, c, k == 1, have_x64);
             else
-                k3_sweep32<kAddPsi3, 2><<<g2, kNodeBlock, 0, s>>>(m, st->phys, b, cur, prv, a, c, k == 1, have_x64);
+                k3_sweep32<kAddPsi3><<<gc, kCoopBlock, 0, s>>>(m, st->phys, b, cur, prv, a, c, k == 1, have_x64);
             std::swap(cur, prv);
         }
         if (r < st->rounds - 1) {
@@ -1388,9 +1453,9 @@ static void enqueue_step_dev32(felbm3d_state* st, cudaStream_t s) {
     mark3(st, s, 1);
     k3_gradmu32<<<grid_for(m.T, kBlock), kBlock, 0, s>>>(m, b);
     mark3(st, s, 2);
-    k3_element32<<<grid_for(m.T, 128), 128, 0, s>>>(m, st->phys, b);
+    k3_element32<<<grid_for(m.T, kElemTets), kCoopBlock, 0, s>>>(m, st->phys, b);
     mark3(st, s, 3);
-    k3_rhs32<<<dim3(grid_for(m.N, kNodeBlock), 2), kNodeBlock, 0, s>>>(m, st->phys, b, (float)st->inv_theta);
+    k3_rhs32<<<grid_for(m.N, kItemsPerBlock), kCoopBlock, 0, s>>>(m, st->phys, b, (float)st->inv_theta);
     mark3(st, s, 4);
     enqueue_solve3(st, s);
     mark3(st, s, 5);

@@ -57,100 +57,201 @@ __global__ void __launch_bounds__(kBlock) k3_gradmu32(DevMesh3 m, Bufs3 b) {
     for (int a = 0; a < 3; ++a) b.gmu32[a * Tp + t] = g[a];
 }
 
+// Lattice vectors and weights of the four directions 4c..4c+3 a lane owns
+// (the padding slot 19 gets zeros).
+struct Dir4 {
+    float ex[4], ey[4], ez[4], w[4];
+};
+__device__ __forceinline__ Dir4 lane_dirs(int c) {
+    Dir4 d;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int q = 4 * c + j;
+        const bool ok = q < 19;
+        d.ex[j] = ok ? (float)ex3(q) : 0.0f;
+        d.ey[j] = ok ? (float)ey3(q) : 0.0f;
+        d.ez[j] = ok ? (float)ez3(q) : 0.0f;
+        d.w[j] = !ok ? 0.0f : q == 0 ? 1.0f / 3.0f : (q <= 6 ? 1.0f / 18.0f : 1.0f / 36.0f);
+    }
+    return d;
+}
+
 // ------------------------------- forces and element residual (FP32) ------
-__global__ void __launch_bounds__(128) k3_element32(DevMesh3 m, Phys3 c, Bufs3 b) {
-    int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= m.T) return;
-    const int Tp = m.Tp, Np = m.Np;
-    int v[4];
-    float bx[4], by[4], bz[4];
+// R_a = V (Phi_a - e_a . grad psi_hat_a), psi_hat = psi^eq + (1 - omega) dpsi,
+// gradients from differences to vertex 0 (the four shape gradients sum to
+// zero).  Two phases per block of kElemTets tetrahedra: (A) one thread per
+// tetrahedron forms the element quantities shared by all directions (the
+// only FP64 work: C differences) into shared memory; (B) five-lane groups
+// take one tetrahedron at a time, lane c its directions 4c..4c+3 of both
+// sets, reading the vertices' deviation rows as whole contiguous rows.
+constexpr int kElemTets = kCoopBlock;
+enum ElemField {
+    EF_V, EF_C0, EF_DC1, EF_DC2, EF_DC3, EF_DP1, EF_DP2, EF_DP3, EF_U0X, EF_U0Y, EF_U0Z,
+    EF_DU1X, EF_DU1Y, EF_DU1Z, EF_DU2X, EF_DU2Y, EF_DU2Z, EF_DU3X, EF_DU3Y, EF_DU3Z,
+    EF_OM0, EF_OM1, EF_OM2, EF_OM3, EF_DSU1, EF_DSU2, EF_DSU3,
+    EF_B1X, EF_B1Y, EF_B1Z, EF_B2X, EF_B2Y, EF_B2Z, EF_B3X, EF_B3Y, EF_B3Z,
+    EF_UBX, EF_UBY, EF_UBZ, EF_MUB, EF_UUB, EF_UU0, EF_RHO0, EF_GRX, EF_GRY, EF_GRZ, EF_GCX, EF_GCY, EF_GCZ,
+    EF_VHX, EF_VHY, EF_VHZ, EF_UGR, EF_UGC, EF_UVH, EF_MLAP, EF_COUNT
+};
+
+__global__ void __launch_bounds__(kCoopBlock) k3_element32(DevMesh3 m, Phys3 c, Bufs3 b) {
+    __shared__ float rec[EF_COUNT][kElemTets];
+    __shared__ int vid[4][kElemTets];
+    const int t0 = blockIdx.x * kElemTets, Tp = m.Tp;
+    const int nt = min(kElemTets, m.T - t0);
+    // ---- phase A: element quantities, one thread per tetrahedron
+    if ((int)threadIdx.x < nt) {
+        const int r = threadIdx.x, t = t0 + r;
+        int v[4];
+        float bx[4], by[4], bz[4];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        v[k] = m.tet[k * Tp + t];
-        bx[k] = m.grad32[(3 * k) * Tp + t];
-        by[k] = m.grad32[(3 * k + 1) * Tp + t];
-        bz[k] = m.grad32[(3 * k + 2) * Tp + t];
-    }
-    const float V = m.vol32[t];
-    const double C0d = b.C[v[0]];
-    const float C0 = (float)C0d;
-    float dC[4], p[4], ux[4], uy[4], uz[4], om1[4];
-    float mus = 0.0f;
+        for (int n = 0; n < 4; ++n) {
+            v[n] = m.tet[n * Tp + t];
+            bx[n] = m.grad32[(3 * n) * Tp + t];
+            by[n] = m.grad32[(3 * n + 1) * Tp + t];
+            bz[n] = m.grad32[(3 * n + 2) * Tp + t];
+            vid[n][r] = v[n];
+        }
+        const double C0d = b.C[v[0]];
+        const float C0 = (float)C0d;
+        float dC[4], p[4], ux[4], uy[4], uz[4];
+        float mus = 0.0f;
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        dC[k] = k == 0 ? 0.0f : (float)(b.C[v[k]] - C0d);
-        p[k] = b.p32[v[k]];
-        ux[k] = b.ux32[v[k]];
-        uy[k] = b.uy32[v[k]];
-        uz[k] = b.uz32[v[k]];
-        mus += b.mu32[v[k]];
-        om1[k] = 1.0f - omega32_3(C0 + dC[k], c);
-    }
-    const float Cb = C0 + 0.25f * (dC[1] + dC[2] + dC[3]);
-    const float ubx = 0.25f * (ux[0] + ux[1] + ux[2] + ux[3]);
-    const float uby = 0.25f * (uy[0] + uy[1] + uy[2] + uy[3]);
-    const float ubz = 0.25f * (uz[0] + uz[1] + uz[2] + uz[3]);
-    const float mub = 0.25f * mus;
-    float gC[3] = {0.0f, 0.0f, 0.0f}, gp[3] = {0.0f, 0.0f, 0.0f};
+        for (int n = 0; n < 4; ++n) {
+            dC[n] = n == 0 ? 0.0f : (float)(b.C[v[n]] - C0d);
+            p[n] = b.p32[v[n]];
+            ux[n] = b.ux32[v[n]];
+            uy[n] = b.uy32[v[n]];
+            uz[n] = b.uz32[v[n]];
+            mus += b.mu32[v[n]];
+            rec[EF_OM0 + n][r] = 1.0f - omega32_3(C0 + dC[n], c);
+        }
+        const float Cb = C0 + 0.25f * (dC[1] + dC[2] + dC[3]);
+        const float ubx = 0.25f * (ux[0] + ux[1] + ux[2] + ux[3]);
+        const float uby = 0.25f * (uy[0] + uy[1] + uy[2] + uy[3]);
+        const float ubz = 0.25f * (uz[0] + uz[1] + uz[2] + uz[3]);
+        const float mub = 0.25f * mus;
+        float gC[3] = {0.0f, 0.0f, 0.0f}, gp[3] = {0.0f, 0.0f, 0.0f};
 #pragma unroll
-    for (int k = 1; k < 4; ++k) {
-        const float dp = p[k] - p[0];
-        gC[0] = fmaf(dC[k], bx[k], gC[0]);
-        gC[1] = fmaf(dC[k], by[k], gC[1]);
-        gC[2] = fmaf(dC[k], bz[k], gC[2]);
-        gp[0] = fmaf(dp, bx[k], gp[0]);
-        gp[1] = fmaf(dp, by[k], gp[1]);
-        gp[2] = fmaf(dp, bz[k], gp[2]);
-    }
-    const float gm0 = b.gmu32[t], gm1 = b.gmu32[Tp + t], gm2 = b.gmu32[2 * Tp + t];
-    float flux = 0.0f;
+        for (int n = 1; n < 4; ++n) {
+            const float dp = p[n] - p[0];
+            gC[0] = fmaf(dC[n], bx[n], gC[0]);
+            gC[1] = fmaf(dC[n], by[n], gC[1]);
+            gC[2] = fmaf(dC[n], bz[n], gC[2]);
+            gp[0] = fmaf(dp, bx[n], gp[0]);
+            gp[1] = fmaf(dp, by[n], gp[1]);
+            gp[2] = fmaf(dp, bz[n], gp[2]);
+            const float dx = ux[n] - ux[0], dy = uy[n] - uy[0], dz = uz[n] - uz[0];
+            rec[EF_DC1 + n - 1][r] = dC[n];
+            rec[EF_DP1 + n - 1][r] = dp;
+            rec[EF_DU1X + 3 * (n - 1)][r] = dx;
+            rec[EF_DU1X + 3 * (n - 1) + 1][r] = dy;
+            rec[EF_DU1X + 3 * (n - 1) + 2][r] = dz;
+            rec[EF_DSU1 + n - 1][r] = dx * (ux[n] + ux[0]) + dy * (uy[n] + uy[0]) + dz * (uz[n] + uz[0]);
+            rec[EF_B1X + 3 * (n - 1)][r] = bx[n];
+            rec[EF_B1X + 3 * (n - 1) + 1][r] = by[n];
+            rec[EF_B1X + 3 * (n - 1) + 2][r] = bz[n];
+        }
+        const float gm0 = b.gmu32[t], gm1 = b.gmu32[Tp + t], gm2 = b.gmu32[2 * Tp + t];
+        float flux = 0.0f;
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        int nb = m.nbr[k * Tp + t];
-        if (nb >= 0)
-            flux += (gm0 + b.gmu32[nb]) * bx[k] + (gm1 + b.gmu32[Tp + nb]) * by[k] + (gm2 + b.gmu32[2 * Tp + nb]) * bz[k];
+        for (int n = 0; n < 4; ++n) {
+            const int nb = m.nbr[n * Tp + t];
+            if (nb >= 0)
+                flux += (gm0 + b.gmu32[nb]) * bx[n] + (gm1 + b.gmu32[Tp + nb]) * by[n] + (gm2 + b.gmu32[2 * Tp + nb]) * bz[n];
+        }
+        const float drho = c.drho_f;
+        const float rhob = c.rho_v_f + Cb * drho;
+        const float f = 3.0f * Cb / rhob;
+        const float gr[3] = {drho * gC[0], drho * gC[1], drho * gC[2]};
+        const float vh[3] = {gC[0] - f * (gp[0] - mub * gC[0]), gC[1] - f * (gp[1] - mub * gC[1]),
+                             gC[2] - f * (gp[2] - mub * gC[2])};
+        rec[EF_V][r] = m.vol32[t];
+        rec[EF_C0][r] = C0;
+        rec[EF_U0X][r] = ux[0];
+        rec[EF_U0Y][r] = uy[0];
+        rec[EF_U0Z][r] = uz[0];
+        rec[EF_UBX][r] = ubx;
+        rec[EF_UBY][r] = uby;
+        rec[EF_UBZ][r] = ubz;
+        rec[EF_MUB][r] = mub;
+        rec[EF_UUB][r] = 1.5f * (ubx * ubx + uby * uby + ubz * ubz);
+        rec[EF_UU0][r] = 1.5f * (ux[0] * ux[0] + uy[0] * uy[0] + uz[0] * uz[0]);
+        rec[EF_RHO0][r] = c.rho_v_f + C0 * drho;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            rec[EF_GRX + a][r] = gr[a];
+            rec[EF_GCX + a][r] = gC[a];
+            rec[EF_VHX + a][r] = vh[a];
+        }
+        rec[EF_UGR][r] = ubx * gr[0] + uby * gr[1] + ubz * gr[2];
+        rec[EF_UGC][r] = ubx * gC[0] + uby * gC[1] + ubz * gC[2];
+        rec[EF_UVH][r] = ubx * vh[0] + uby * vh[1] + ubz * vh[2];
+        rec[EF_MLAP][r] = c.mobility_f * (-1.5f * flux);
     }
-    const float Mlap = c.mobility_f * (-1.5f * flux);
+    __syncthreads();
+    // ---- phase B: directions, five lanes per tetrahedron
+    const int lane = threadIdx.x & 31, grp = lane / kGroup, cl = lane - grp * kGroup;
+    if (grp >= kGroupsPerWarp) return;
+    const int g = (threadIdx.x >> 5) * kGroupsPerWarp + grp;          // 0..23
+    constexpr int kGroups = kGroupsPerWarp * (kCoopBlock / 32);
+    const Dir4 d = lane_dirs(cl);
     const float drho = c.drho_f;
-    const float rhob = c.rho_v_f + Cb * drho;
-    const float rho0 = c.rho_v_f + C0 * drho;
-    const float gr[3] = {drho * gC[0], drho * gC[1], drho * gC[2]};
-    const float f = 3.0f * Cb / rhob;
-    const float vh[3] = {gC[0] - f * (gp[0] - mub * gC[0]), gC[1] - f * (gp[1] - mub * gC[1]),
-                         gC[2] - f * (gp[2] - mub * gC[2])};
-    const float u_gr = ubx * gr[0] + uby * gr[1] + ubz * gr[2];
-    const float u_gC = ubx * gC[0] + uby * gC[1] + ubz * gC[2];
-    const float u_vh = ubx * vh[0] + uby * vh[1] + ubz * vh[2];
-    const float uub15 = 1.5f * (ubx * ubx + uby * uby + ubz * ubz);
-    const float uu0 = 1.5f * (ux[0] * ux[0] + uy[0] * uy[0] + uz[0] * uz[0]);
-    float* dst = b.R32 + (size_t)t * kR32;
+    for (int r = g; r < nt; r += kGroups) {
+        const float V = rec[EF_V][r], C0 = rec[EF_C0][r];
+        const float u0x = rec[EF_U0X][r], u0y = rec[EF_U0Y][r], u0z = rec[EF_U0Z][r];
+        const float ubx = rec[EF_UBX][r], uby = rec[EF_UBY][r], ubz = rec[EF_UBZ][r];
+        const float mub = rec[EF_MUB][r], uub15 = rec[EF_UUB][r], uu0 = rec[EF_UU0][r], rho0 = rec[EF_RHO0][r];
+        const float u_gr = rec[EF_UGR][r], u_gC = rec[EF_UGC][r], u_vh = rec[EF_UVH][r], Mlap = rec[EF_MLAP][r];
+        float4 gk[4], hk[4];
 #pragma unroll
-    for (int q = 0; q < 19; ++q) {
-        const float w = (float)wq3(q);
-        const float G = gamma32_3(q, ubx, uby, ubz, uub15);
-        const float phig = (1.0f / 3.0f) * (G - w) * (edot3(q, gr[0], gr[1], gr[2]) - u_gr) +
-                           mub * G * (edot3(q, gC[0], gC[1], gC[2]) - u_gC);
-        const float phih = ((edot3(q, vh[0], vh[1], vh[2]) - u_vh) + Mlap) * G;
-        float dg = 0.0f, dh = 0.0f;
-        if (q != 0) {
-            const float G0 = gamma32_3(q, ux[0], uy[0], uz[0], uu0);
-            const float g0 = om1[0] * b.dpsi[q * Np + v[0]], h0 = om1[0] * b.dpsi[(19 + q) * Np + v[0]];
+        for (int n = 0; n < 4; ++n) {
+            const float4* row = reinterpret_cast<const float4*>(b.dpsi + (size_t)vid[n][r] * kRow);
+            gk[n] = row[cl];
+            hk[n] = row[5 + cl];
+        }
+        float4 og = make_float4(0.0f, 0.0f, 0.0f, 0.0f), oh = og;
 #pragma unroll
-            for (int k = 1; k < 4; ++k) {
-                const float dG = dgamma32_3(q, ux[k] - ux[0], uy[k] - uy[0], uz[k] - uz[0], ux[k] + ux[0],
-                                            uy[k] + uy[0], uz[k] + uz[0]);
+        for (int j = 0; j < 4; ++j) {
+            const float ex = d.ex[j], ey = d.ey[j], ez = d.ez[j], w = d.w[j];
+            const float eu = ex * ubx + ey * uby + ez * ubz;
+            const float G = w * (1.0f + 3.0f * eu + 4.5f * eu * eu - uub15);
+            const float egr = ex * rec[EF_GRX][r] + ey * rec[EF_GRY][r] + ez * rec[EF_GRZ][r];
+            const float egc = ex * rec[EF_GCX][r] + ey * rec[EF_GCY][r] + ez * rec[EF_GCZ][r];
+            const float evh = ex * rec[EF_VHX][r] + ey * rec[EF_VHY][r] + ez * rec[EF_VHZ][r];
+            const float phig = (1.0f / 3.0f) * (G - w) * (egr - u_gr) + mub * G * (egc - u_gC);
+            const float phih = ((evh - u_vh) + Mlap) * G;
+            const float e0 = ex * u0x + ey * u0y + ez * u0z;
+            const float G0 = w * (1.0f + 3.0f * e0 + 4.5f * e0 * e0 - uu0);
+            const float om0 = rec[EF_OM0][r];
+            const float g0 = om0 * comp(gk[0], j), h0 = om0 * comp(hk[0], j);
+            float dg = 0.0f, dh = 0.0f;
+#pragma unroll
+            for (int n = 1; n < 4; ++n) {
+                const float dx = rec[EF_DU1X + 3 * (n - 1)][r], dy = rec[EF_DU1X + 3 * (n - 1) + 1][r],
+                            dz = rec[EF_DU1X + 3 * (n - 1) + 2][r];
+                const float edu = ex * dx + ey * dy + ez * dz;
+                const float esu = edu + 2.0f * e0;                    // e.(u_n + u_0)
+                const float dG = w * (3.0f * edu + 4.5f * edu * esu - 1.5f * rec[EF_DSU1 + n - 1][r]);
+                const float dCn = rec[EF_DC1 + n - 1][r];
                 // differences of the equilibria and of the post-collision deviations to vertex 0
-                const float dhe = (G0 + dG) * dC[k] + C0 * dG;
-                const float dge = w * (p[k] - p[0]) + (1.0f / 3.0f) * (drho * dC[k] * (G0 + dG - w) + rho0 * dG);
-                const float dgd = om1[k] * b.dpsi[q * Np + v[k]] - g0;
-                const float dhd = om1[k] * b.dpsi[(19 + q) * Np + v[k]] - h0;
-                const float eb = edot3(q, bx[k], by[k], bz[k]);
+                const float dhe = (G0 + dG) * dCn + C0 * dG;
+                const float dge = w * rec[EF_DP1 + n - 1][r] + (1.0f / 3.0f) * (drho * dCn * (G0 + dG - w) + rho0 * dG);
+                const float omn = rec[EF_OM0 + n][r];
+                const float dgd = omn * comp(gk[n], j) - g0;
+                const float dhd = omn * comp(hk[n], j) - h0;
+                const float eb = ex * rec[EF_B1X + 3 * (n - 1)][r] + ey * rec[EF_B1X + 3 * (n - 1) + 1][r] +
+                                 ez * rec[EF_B1X + 3 * (n - 1) + 2][r];
                 dg = fmaf(dge + dgd, eb, dg);
                 dh = fmaf(dhe + dhd, eb, dh);
             }
+            // the padding direction has w = 0 and e = 0: its residual is 0
+            set_comp(og, j, V * (phig - dg));
+            set_comp(oh, j, V * (phih - dh));
         }
-        dst[q] = V * (phig - dg);
-        dst[19 + q] = V * (phih - dh);
+        float4* dst = reinterpret_cast<float4*>(b.R32 + (size_t)(t0 + r) * kRow);
+        dst[cl] = og;
+        dst[5 + cl] = oh;
     }
 }
 
@@ -158,61 +259,73 @@ __global__ void __launch_bounds__(128) k3_element32(DevMesh3 m, Phys3 c, Bufs3 b
 // As k3_rhs; the wall term needs psi_hat_opp - psi_hat at a node, which in
 // the split form is  g: -2 w rho (e.u) + (1-omega)(dg_opp - dg),
 //                    h: -6 w C (e.u)   + (1-omega)(dh_opp - dh).
-__device__ __forceinline__ float wall_diff32(const DevMesh3& m, const Phys3& c, const Bufs3& b, int s, int q, int v) {
-    const int Np = m.Np;
+__device__ __forceinline__ float wall_diff32(const Phys3& c, const Bufs3& b, int s, int q, int v, float ex, float ey,
+                                             float ez, float w) {
     const float C = (float)b.C[v];
-    const float eu = edot3(q, b.ux32[v], b.uy32[v], b.uz32[v]);
+    const float eu = ex * b.ux32[v] + ey * b.uy32[v] + ez * b.uz32[v];
     const float om1 = 1.0f - omega32_3(C, c);
-    const float w = (float)wq3(q);
-    const float* d = b.dpsi + (size_t)19 * s * Np;
-    const float ddev = om1 * (d[opp3(q) * Np + v] - d[q * Np + v]);
+    const float* d = b.dpsi + (size_t)v * kRow + slot(s, 0);
+    const float ddev = om1 * (d[opp3(q)] - d[q]);
     const float eq = s == 0 ? -2.0f * w * (c.rho_v_f + C * c.drho_f) * eu : -6.0f * w * C * eu;
     return eq + ddev;
 }
 
-__global__ void __launch_bounds__(kNodeBlock) k3_rhs32(DevMesh3 m, Phys3 c, Bufs3 b, float inv_theta) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= m.N) return;
-    const int s = blockIdx.y, Np = m.Np, ninc = m.ninc;
-    float acc[19];
-#pragma unroll
-    for (int q = 0; q < 19; ++q) acc[q] = 0.0f;
+__global__ void __launch_bounds__(kCoopBlock) k3_rhs32(DevMesh3 m, Phys3 c, Bufs3 b, float inv_theta) {
+    const Coop k = coop_index(m.N);
+    if (!k.active) return;
+    const int i = k.item, ninc = m.ninc;
+    const Dir4 d = lane_dirs(k.c);
+    float4 ag = make_float4(0.0f, 0.0f, 0.0f, 0.0f), ah = ag;
     const float c1 = c.dt4_f, c2 = c.dt2h_f;
-    for (int k = m.inc_ptr[i]; k < m.inc_ptr[i + 1]; ++k) {
-        const float* src = b.R32 + (size_t)m.inc_tet[k] * kR32 + 19 * s;
-        const float bxi = m.inc_b32[k], byi = m.inc_b32[ninc + k], bzi = m.inc_b32[2 * ninc + k];
+    for (int e = m.inc_ptr[i]; e < m.inc_ptr[i + 1]; ++e) {
+        const float4* row = reinterpret_cast<const float4*>(b.R32 + (size_t)m.inc_tet[e] * kRow);
+        const float bxi = m.inc_b32[e], byi = m.inc_b32[ninc + e], bzi = m.inc_b32[2 * ninc + e];
+        const float4 rg = row[k.c], rh = row[5 + k.c];
 #pragma unroll
-        for (int q = 0; q < 19; ++q) acc[q] = fmaf(src[q], c1 + c2 * edot3(q, bxi, byi, bzi), acc[q]);
+        for (int j = 0; j < 4; ++j) {
+            const float w = c1 + c2 * (d.ex[j] * bxi + d.ey[j] * byi + d.ez[j] * bzi);
+            set_comp(ag, j, fmaf(comp(rg, j), w, comp(ag, j)));
+            set_comp(ah, j, fmaf(comp(rh, j), w, comp(ah, j)));
+        }
     }
     const int F = m.F;
-    for (int k = m.winc_ptr[i]; k < m.winc_ptr[i + 1]; ++k) {
-        const int f = m.winc_face[k];
-        int o[2], n = 0;
+    for (int e = m.winc_ptr[i]; e < m.winc_ptr[i + 1]; ++e) {
+        const int f = m.winc_face[e];
+        int o0 = -1, o1 = -1;
 #pragma unroll
         for (int cc = 0; cc < 3; ++cc) {
-            int vv = m.wall_v[cc * F + f];
-            if (vv != i && n < 2) o[n++] = vv;
+            const int vv = m.wall_v[cc * F + f];
+            if (vv != i) {
+                if (o0 < 0)
+                    o0 = vv;
+                else
+                    o1 = vv;
+            }
         }
         const float A = (float)m.wall_area[f];
         const float nx = (float)m.wall_n[f], ny = (float)m.wall_n[F + f], nz = (float)m.wall_n[2 * F + f];
 #pragma unroll
-        for (int q = 1; q < 19; ++q) {
-            const float en = edot3(q, nx, ny, nz);
-            if (en < 0.0f) {
-                const float di = wall_diff32(m, c, b, s, q, i);
-                const float d1 = wall_diff32(m, c, b, s, q, o[0]);
-                const float d2 = wall_diff32(m, c, b, s, q, o[1]);
-                acc[q] += -c.dt_f * en * (A * (1.0f / 6.0f) * di + A * (1.0f / 12.0f) * (d1 + d2));
-            }
+        for (int j = 0; j < 4; ++j) {
+            const int q = 4 * k.c + j;
+            const float en = d.ex[j] * nx + d.ey[j] * ny + d.ez[j] * nz;
+            if (q == 0 || q >= 19 || !(en < 0.0f)) continue;
+            const float fa = -c.dt_f * en * A * (1.0f / 6.0f), fb = -c.dt_f * en * A * (1.0f / 12.0f);
+            const float ex = d.ex[j], ey = d.ey[j], ez = d.ez[j], w = d.w[j];
+            const float addg = fa * wall_diff32(c, b, 0, q, i, ex, ey, ez, w) +
+                               fb * (wall_diff32(c, b, 0, q, o0, ex, ey, ez, w) + wall_diff32(c, b, 0, q, o1, ex, ey, ez, w));
+            const float addh = fa * wall_diff32(c, b, 1, q, i, ex, ey, ez, w) +
+                               fb * (wall_diff32(c, b, 1, q, o0, ex, ey, ez, w) + wall_diff32(c, b, 1, q, o1, ex, ey, ez, w));
+            set_comp(ag, j, comp(ag, j) + addg);
+            set_comp(ah, j, comp(ah, j) + addh);
         }
     }
     const float sc = m.inv_lumped32[i] * inv_theta;
-#pragma unroll
-    for (int q = 0; q < 19; ++q) {
-        const size_t r = (size_t)(19 * s + q) * Np + i;
-        b.r32[r] = acc[q];
-        b.e1[r] = acc[q] * sc;
-    }
+    float4* r4 = reinterpret_cast<float4*>(b.r32 + (size_t)i * kRow);
+    float4* e4 = reinterpret_cast<float4*>(b.e1 + (size_t)i * kRow);
+    r4[k.c] = ag;
+    r4[5 + k.c] = ah;
+    e4[k.c] = make_float4(ag.x * sc, ag.y * sc, ag.z * sc, ag.w * sc);
+    e4[5 + k.c] = make_float4(ah.x * sc, ah.y * sc, ah.z * sc, ah.w * sc);
 }
 
 // ------------------------------------------- field and deviation update ----
@@ -222,17 +335,27 @@ __global__ void __launch_bounds__(kNodeBlock) k3_rhs32(DevMesh3 m, Phys3 c, Bufs
 //   dpsi' = (1 - omega) dpsi + d - (psi^eq(n+1) - psi^eq(n)),
 //   h^eq' - h^eq = Gamma dC + C' dGamma,
 //   g^eq' - g^eq = w dp + (drho dC (Gamma - w) + rho' dGamma) / 3.
-__device__ void dev32_update3(const DevMesh3& m, const Phys3& c, const Bufs3& b, int i, const float* d) {
-    const int Np = m.Np;
+// Called by every lane of the warp (the group sums are shuffles); lane c
+// holds the increments of directions 4c..4c+3 (dg, dh).
+__device__ void dev32_update3(const DevMesh3& m, const Phys3& c, const Bufs3& b, const Coop& k, int i,
+                              const float4& dg, const float4& dh) {
+    const Dir4 d = lane_dirs(k.c);
     float sg = 0.0f, sh = 0.0f, mx = 0.0f, my = 0.0f, mz = 0.0f;
 #pragma unroll
-    for (int q = 0; q < 19; ++q) {
-        sg += d[q];
-        sh += d[19 + q];
-        mx += edot3(q, d[q], 0.0f, 0.0f);
-        my += edot3(q, 0.0f, d[q], 0.0f);
-        mz += edot3(q, 0.0f, 0.0f, d[q]);
+    for (int j = 0; j < 4; ++j) {       // padding slots hold zero increments
+        const float x = comp(dg, j);
+        sg += x;
+        sh += comp(dh, j);
+        mx = fmaf(d.ex[j], x, mx);
+        my = fmaf(d.ey[j], x, my);
+        mz = fmaf(d.ez[j], x, mz);
     }
+    sg = group_sum(sg, k);
+    sh = group_sum(sh, k);
+    mx = group_sum(mx, k);
+    my = group_sum(my, k);
+    mz = group_sum(mz, k);
+    if (!k.active) return;
     const double Cd = b.C[i];
     const double Cnd = Cd + (double)sh;
     const float C = (float)Cd, dC = sh;
@@ -244,22 +367,32 @@ __device__ void dev32_update3(const DevMesh3& m, const Phys3& c, const Bufs3& b,
     const float om1 = 1.0f - omega32_3(C, c);
     const float uu15 = 1.5f * (ux * ux + uy * uy + uz * uz);
     const float dux = uxn - ux, duy = uyn - uy, duz = uzn - uz, sux = uxn + ux, suy = uyn + uy, suz = uzn + uz;
+    const float dsu = dux * sux + duy * suy + duz * suz;
     const float Cn = (float)Cnd, drho = c.drho_f * dC;
+    float4* row = reinterpret_cast<float4*>(b.dpsi + (size_t)i * kRow);
+    float4 og = row[k.c], oh = row[5 + k.c];
 #pragma unroll
-    for (int q = 0; q < 19; ++q) {
-        const float w = (float)wq3(q);
-        const float G = gamma32_3(q, ux, uy, uz, uu15);
-        const float dG = dgamma32_3(q, dux, duy, duz, sux, suy, suz);
+    for (int j = 0; j < 4; ++j) {
+        if (4 * k.c + j >= 19) continue;
+        const float ex = d.ex[j], ey = d.ey[j], ez = d.ez[j], w = d.w[j];
+        const float eu = ex * ux + ey * uy + ez * uz;
+        const float G = w * (1.0f + 3.0f * eu + 4.5f * eu * eu - uu15);
+        const float edu = ex * dux + ey * duy + ez * duz, esu = ex * sux + ey * suy + ez * suz;
+        const float dG = w * (3.0f * edu + 4.5f * edu * esu - 1.5f * dsu);
         const float dgeq = w * sg + (1.0f / 3.0f) * (drho * (G - w) + rho_n * dG);
         const float dheq = G * dC + Cn * dG;
-        b.dpsi[q * Np + i] = om1 * b.dpsi[q * Np + i] + d[q] - dgeq;
-        b.dpsi[(19 + q) * Np + i] = om1 * b.dpsi[(19 + q) * Np + i] + d[19 + q] - dheq;
+        set_comp(og, j, om1 * comp(og, j) + comp(dg, j) - dgeq);
+        set_comp(oh, j, om1 * comp(oh, j) + comp(dh, j) - dheq);
     }
-    b.C[i] = Cnd;
-    b.p32[i] = b.p32[i] + sg;
-    b.ux32[i] = uxn;
-    b.uy32[i] = uyn;
-    b.uz32[i] = uzn;
+    row[k.c] = og;
+    row[5 + k.c] = oh;
+    if (k.c == 0) {
+        b.C[i] = Cnd;
+        b.p32[i] = b.p32[i] + sg;
+        b.ux32[i] = uxn;
+        b.uy32[i] = uyn;
+        b.uz32[i] = uzn;
+    }
 }
 
 // ---------------------------------------------- conversions (FP64 I/O) ----
@@ -271,11 +404,12 @@ __global__ void k3_dev32_to_stage(DevMesh3 m, Phys3 c, Bufs3 b) {
     const double C = b.C[i], p = b.p32[i], ux = b.ux32[i], uy = b.uy32[i], uz = b.uz32[i];
     const double rho = c.rho_v + C * (c.rho_l - c.rho_v);
     const double uu15 = 1.5 * (ux * ux + uy * uy + uz * uz);
+    const float* d = b.dpsi + (size_t)i * kRow;
     for (int q = 0; q < 19; ++q) {
         double eu = edot3(q, ux, uy, uz);
         double G = wq3(q) * (1.0 + 3.0 * eu + 4.5 * eu * eu - uu15);
-        b.stage[(size_t)q * N + o] = wq3(q) * p + rho * (1.0 / 3.0) * (G - wq3(q)) + (double)b.dpsi[q * m.Np + i];
-        b.stage[(size_t)(19 + q) * N + o] = G * C + (double)b.dpsi[(19 + q) * m.Np + i];
+        b.stage[(size_t)q * N + o] = wq3(q) * p + rho * (1.0 / 3.0) * (G - wq3(q)) + (double)d[slot(0, q)];
+        b.stage[(size_t)(19 + q) * N + o] = G * C + (double)d[slot(1, q)];
     }
 }
 
@@ -296,12 +430,15 @@ __global__ void k3_stage_to_dev32(DevMesh3 m, Phys3 c, Bufs3 b) {
     const double rho = c.rho_v + C * (c.rho_l - c.rho_v);
     const double ux = 3.0 * mx / rho, uy = 3.0 * my / rho, uz = 3.0 * mz / rho;
     const double uu15 = 1.5 * (ux * ux + uy * uy + uz * uz);
+    float* d = b.dpsi + (size_t)i * kRow;
     for (int q = 0; q < 19; ++q) {
         double eu = edot3(q, ux, uy, uz);
         double G = wq3(q) * (1.0 + 3.0 * eu + 4.5 * eu * eu - uu15);
-        b.dpsi[q * m.Np + i] = (float)(b.stage[(size_t)q * N + o] - (wq3(q) * p + rho * (1.0 / 3.0) * (G - wq3(q))));
-        b.dpsi[(19 + q) * m.Np + i] = (float)(b.stage[(size_t)(19 + q) * N + o] - G * C);
+        d[slot(0, q)] = (float)(b.stage[(size_t)q * N + o] - (wq3(q) * p + rho * (1.0 / 3.0) * (G - wq3(q))));
+        d[slot(1, q)] = (float)(b.stage[(size_t)(19 + q) * N + o] - G * C);
     }
+    d[slot(0, 19)] = 0.0f;
+    d[slot(1, 19)] = 0.0f;
     b.C[i] = C;
     b.p32[i] = (float)p;
     b.ux32[i] = (float)ux;
@@ -319,5 +456,5 @@ __global__ void k3_init_dev32(DevMesh3 m, Bufs3 b) {
     b.uy32[i] = 0.0f;
     b.uz32[i] = 0.0f;
     b.mu32[i] = 0.0f;
-    for (int q = 0; q < 38; ++q) b.dpsi[q * m.Np + i] = 0.0f;
+    for (int q = 0; q < kRow; ++q) b.dpsi[(size_t)i * kRow + q] = 0.0f;
 }
