@@ -551,20 +551,39 @@ __global__ void __launch_bounds__(kNodeBlock) k3_refine(DevMesh3 m, Bufs3 b, con
 __device__ void dev32_update3(const DevMesh3& m, const Phys3& c, const Bufs3& b, const Coop& k, int i,
                               const float4& dg, const float4& dh);
 
-template <int kFinal>
+__device__ __forceinline__ void pdl_wait3() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_release3() { asm volatile("griddepcontrol.launch_dependents;" :::); }
+
+// kW > 0: ELL of that width, its columns and values loaded up front (they
+// do not depend on the previous sweep, so under programmatic dependent
+// launch they are fetched while that sweep drains); kW = 0: CSR.
+template <int kFinal, int kW>
 __global__ void __launch_bounds__(kCoopBlock) k3_sweep32(DevMesh3 m, Phys3 c, Bufs3 b, const float* __restrict__ cur,
                                                          float* prev, float a, float cc, int first, int have_x64) {
+    pdl_release3();
     const Coop k = coop_index(m.N);
     const int i = k.active ? k.item : 0;      // idle lanes read node 0 and write nothing
     const int Np = m.Np;
+    constexpr int kWr = kW > 0 ? kW : 1;
+    int col[kWr];
+    float val[kWr];
+    if (kW > 0 && k.active) {
+#pragma unroll
+        for (int e = 0; e < kWr; ++e) {
+            col[e] = m.ell_col[e * Np + i];
+            val[e] = m.ell_val[e * Np + i];
+        }
+    }
+    const float sc = cc * m.inv_lumped32[i];
+    pdl_wait3();
     float4 ag = make_float4(0.0f, 0.0f, 0.0f, 0.0f), ah = ag;
     if (k.active) {
-        if (m.ell_w > 0) {
-            for (int e = 0; e < m.ell_w; ++e) {
-                const float4* row = reinterpret_cast<const float4*>(cur + (size_t)m.ell_col[e * Np + i] * kRow);
-                const float v = m.ell_val[e * Np + i];
-                fma4(ag, v, row[k.c]);
-                fma4(ah, v, row[5 + k.c]);
+        if (kW > 0) {
+#pragma unroll
+            for (int e = 0; e < kWr; ++e) {
+                const float4* row = reinterpret_cast<const float4*>(cur + (size_t)col[e] * kRow);
+                fma4(ag, val[e], row[k.c]);
+                fma4(ah, val[e], row[5 + k.c]);
             }
         } else {
             for (int e = m.row_ptr[i]; e < m.row_ptr[i + 1]; ++e) {
@@ -575,7 +594,6 @@ __global__ void __launch_bounds__(kCoopBlock) k3_sweep32(DevMesh3 m, Phys3 c, Bu
             }
         }
     }
-    const float sc = cc * m.inv_lumped32[i];
     const size_t own = (size_t)i * kRow;
     const float4* xk4 = reinterpret_cast<const float4*>(cur + own);
     const float4* xm4 = reinterpret_cast<const float4*>(prev + own);
@@ -791,7 +809,12 @@ struct Carver3 {
 
 static size_t pad64(size_t n) { return (n + 63) & ~size_t(63); }
 
-static int ell_width3(const HostMesh3D& h) { return h.max_degree <= 32 ? h.max_degree : 0; }
+// ELL widths with a compiled sweep: the longest row rounded up; 0 (CSR) beyond 32.
+static int ell_width3(const HostMesh3D& h) {
+    for (int w : {15, 16, 24, 32})
+        if (h.max_degree <= w) return w;
+    return 0;
+}
 
 // Workspace layout; with base == nullptr only the size is computed.
 static size_t carve3(const HostMesh3D& h, bool dev32, void* base, DevMesh3* dm, Bufs3* bo) {
@@ -905,10 +928,42 @@ struct felbm3d_state {
     bool dev32 = false;
     bool timing = false;
     bool timed_step_ran = false;
+    bool use_pdl = true;   // programmatic dependent launch between solve sweeps (FELBM_PDL=0: off)
     cudaEvent_t ev[6] = {};
 };
 
 namespace felbm3 {
+
+template <typename... KArgs, typename... Args>
+static void launch3(bool pdl, void (*kern)(KArgs...), unsigned grid, unsigned block, cudaStream_t s, Args&&... args) {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
+}
+
+// One FP32 sweep with the compiled ELL width of the mesh (else CSR); pdl:
+// the previous launch on the stream is a sweep.
+template <int kFinal>
+static void launch_sweep3(felbm3d_state* st, cudaStream_t s, const float* cur, float* prv, float a, float c, int first,
+                          int have_x64, bool pdl) {
+    const DevMesh3& m = st->dm;
+    const unsigned g = grid_for(m.N, kItemsPerBlock);
+    pdl = pdl && st->use_pdl;
+    switch (m.ell_w) {
+        case 15: launch3(pdl, k3_sweep32<kFinal, 15>, g, kCoopBlock, s, m, st->phys, st->buf, cur, prv, a, c, first, have_x64); break;
+        case 16: launch3(pdl, k3_sweep32<kFinal, 16>, g, kCoopBlock, s, m, st->phys, st->buf, cur, prv, a, c, first, have_x64); break;
+        case 24: launch3(pdl, k3_sweep32<kFinal, 24>, g, kCoopBlock, s, m, st->phys, st->buf, cur, prv, a, c, first, have_x64); break;
+        case 32: launch3(pdl, k3_sweep32<kFinal, 32>, g, kCoopBlock, s, m, st->phys, st->buf, cur, prv, a, c, first, have_x64); break;
+        default: launch3(pdl, k3_sweep32<kFinal, 0>, g, kCoopBlock, s, m, st->phys, st->buf, cur, prv, a, c, first, have_x64);
+    }
+}
 
 static int solve_launches3(const felbm3d_state* st) {
     return st->mode == FELBM_SOLVER_FP64 ? st->sweeps - 1 : st->rounds * (st->sweeps - 1) + (st->rounds - 1);
@@ -973,13 +1028,13 @@ static void enqueue_solve3(felbm3d_state* st, cudaStream_t s) {
         for (int k = 1; k < st->sweeps; ++k) {
             const float a = (float)st->cheb_a[k], c = (float)st->cheb_c[k];
             const bool last = r == st->rounds - 1 && k == st->sweeps - 1;
-            const unsigned gc = grid_for(m.N, kItemsPerBlock);
+            const bool pdl = k > 1;   // the previous launch is a sweep of this round
             if (!last)
-                k3_sweep32<kStore3><<<gc, kCoopBlock, 0, s>>>(m, st->phys, b, cur, prv, a, c, k == 1, have_x64);
+                launch_sweep3<kStore3>(st, s, cur, prv, a, c, k == 1, have_x64, pdl);
             else if (st->dev32)
-                k3_sweep32<kUpdateDev3><<<gc, kCoopBlock, 0, s>>>(m, st->phys, b, cur, prv, a, c, k == 1, have_x64);
+                launch_sweep3<kUpdateDev3>(st, s, cur, prv, a, c, k == 1, have_x64, pdl);
             else
-                k3_sweep32<kAddPsi3><<<gc, kCoopBlock, 0, s>>>(m, st->phys, b, cur, prv, a, c, k == 1, have_x64);
+                launch_sweep3<kAddPsi3>(st, s, cur, prv, a, c, k == 1, have_x64, pdl);
             std::swap(cur, prv);
         }
         if (r < st->rounds - 1) {
@@ -1078,6 +1133,7 @@ int felbm3d_init(const felbm3d_mesh* mesh, const felbm_params* params, const dou
     st->prm = *params;
     st->stream = static_cast<cudaStream_t>(stream);
     st->dev32 = dev32;
+    if (const char* env = std::getenv("FELBM_PDL")) st->use_pdl = std::atoi(env) != 0;
     carve3(h, dev32, d_workspace, &st->dm, &st->buf);
     Phys3& ph = st->phys;
     ph.dt = params->dt;
