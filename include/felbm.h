@@ -68,6 +68,19 @@ extern "C" {
 #define FELBM_SOLVER_MIXED 0
 #define FELBM_SOLVER_FP64 1
 
+/* Element Laplacian of mu in the h-force M lap(mu) Gamma (eq:H).
+ * FACE:  Sec. II.D -- flux of the face-averaged element gradients of mu,
+ *        wall faces zero (eqn:bc1).  The paper's form (default).
+ * NODAL: the patch Laplacian of eqn:lapl_int_mp applied to mu with the zero
+ *        wall flux of eqn:bc1 (the lumped P1 Laplacian), averaged over the
+ *        element's vertices.  Not in the paper: the FACE form fed to the
+ *        nodes through M11^-1 M10 has eigenvalues with positive real part on
+ *        jittered meshes (an anti-diffusive Cahn-Hilliard mode that makes
+ *        long runs diverge at rate ~ M dt max Re); this one has none.
+ *        The adjoint (felbm_adjoint_*) supports FACE only. */
+#define FELBM_LAPMU_FACE 0
+#define FELBM_LAPMU_NODAL 1
+
 /* Model constants (Sec. II of the paper, lattice units).
  *  dt              time step (characteristic step eqn::integrated)
  *  tau_l, tau_v    relaxation times of liquid and vapour; 1/tau = C/tau_l + (1-C)/tau_v
@@ -82,7 +95,8 @@ extern "C" {
  *                  bound 2*3^-14 per correction) or in total (FP64, 0 = 32,
  *                  bound 2*3^-32); >= 2
  *  solver_rounds   corrections of the MIXED solve (0 = 3 for FP64 storage,
- *                  1 for FP32_DEV)                                         */
+ *                  1 for FP32_DEV)
+ *  lapmu_mode      FELBM_LAPMU_FACE (default) or FELBM_LAPMU_NODAL          */
 typedef struct felbm_params {
     double dt;
     double tau_l, tau_v;
@@ -96,6 +110,7 @@ typedef struct felbm_params {
     int32_t solver_mode;
     int32_t solver_iters;
     int32_t solver_rounds;
+    int32_t lapmu_mode;
 } felbm_params;
 
 typedef struct felbm_mesh felbm_mesh;

@@ -62,9 +62,10 @@ class OracleParams:
     mobility: float
     phi_c: tuple = field(default_factory=tuple)   # one wetting potential per wall id
     lap_scale: float = 2.0 / 3.0                  # V_k = lap_scale * |patch_k|
+    lapmu: str = "face"                           # element Laplacian of mu: "face" (Sec. II.D) or "nodal"
 
 
-def params_from_physical(phys, lap_mode="consistent"):
+def params_from_physical(phys, lap_mode="consistent", lapmu="face"):
     """kappa, beta and phi_c from sigma, xi and the contact angles.
 
     Sec. II: xi = sqrt(8 kappa / beta) and sigma = sqrt(2 kappa beta) / 6,
@@ -78,7 +79,7 @@ def params_from_physical(phys, lap_mode="consistent"):
     return OracleParams(dt=phys["dt"], tau_l=phys["tau_l"], tau_v=phys["tau_v"],
                         rho_l=phys["rho_l"], rho_v=phys["rho_v"], kappa=kappa,
                         beta=beta, mobility=phys["mobility"], phi_c=phi_c,
-                        lap_scale=(2.0 / 3.0 if lap_mode == "consistent" else 1.0))
+                        lap_scale=(2.0 / 3.0 if lap_mode == "consistent" else 1.0), lapmu=lapmu)
 
 
 def gamma(u):
@@ -294,9 +295,20 @@ class OracleSim:
         return 2.0 * pr.beta * C * (C - 1.0) * (2.0 * C - 1.0) - self.kappa_lap_C(C)
 
     def lap_mu(self, mu):
-        """Element Laplacian of mu (Sec. II.D): flux of grad mu over the three
-        edges, interior edges taking the mean of the two element gradients,
-        wall edges zero (eqn:bc1), divided by the element area."""
+        """Element Laplacian of mu.  "face" (Sec. II.D): flux of grad mu over
+        the three edges, interior edges taking the mean of the two element
+        gradients, wall edges zero (eqn:bc1), divided by the element area.
+        "nodal": the patch Laplacian of eqn:lapl_int_mp applied to mu with the
+        zero wall flux of eqn:bc1 (consistent volume 2/3 |patch|, i.e. the
+        lumped P1 Laplacian), averaged over the element's vertices like the
+        other element means."""
+        if self.prm.lapmu == "nodal":
+            m = self.mesh
+            gmu = m.grad(mu)
+            flux = np.zeros(m.N)
+            for k in range(3):
+                np.add.at(flux, m.tri[:, k], np.sum(gmu * m.nu[:, k], axis=1))
+            return (flux / (2.0 / 3.0 * m.patch_area))[m.tri].mean(axis=1)
         m = self.mesh
         gmu = m.grad(mu)
         out = np.zeros(m.T)

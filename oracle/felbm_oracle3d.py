@@ -47,7 +47,8 @@ Q = 19
 class Params3D:
     """Model constants of Sec. II in lattice units."""
 
-    def __init__(self, dt, tau_l, tau_v, rho_l, rho_v, kappa, beta, mobility, phi_c, lap_scale=0.75):
+    def __init__(self, dt, tau_l, tau_v, rho_l, rho_v, kappa, beta, mobility, phi_c, lap_scale=0.75, lapmu="face"):
+        self.lapmu = lapmu                   # element Laplacian of mu: "face" (Sec. II.D) or "nodal"
         self.dt, self.tau_l, self.tau_v = dt, tau_l, tau_v
         self.rho_l, self.rho_v = rho_l, rho_v
         self.kappa, self.beta, self.mobility = kappa, beta, mobility
@@ -55,7 +56,7 @@ class Params3D:
         self.lap_scale = lap_scale
 
 
-def params_from_physical3d(phys, lap_mode="consistent"):
+def params_from_physical3d(phys, lap_mode="consistent", lapmu="face"):
     """kappa = 3 sigma xi / 2, beta = 12 sigma / xi (interface width xi and
     tension sigma of the double-well free energy, Sec. II); phi_c from
     Young's relation cos(theta) = -phi_c / sqrt(2 kappa beta)."""
@@ -64,7 +65,7 @@ def params_from_physical3d(phys, lap_mode="consistent"):
     root = math.sqrt(2.0 * kappa * beta)
     return Params3D(phys["dt"], phys["tau_l"], phys["tau_v"], phys["rho_l"], phys["rho_v"], kappa, beta,
                     phys["mobility"], [-root * math.cos(math.radians(t)) for t in phys["theta_deg"]],
-                    0.75 if lap_mode == "consistent" else 1.0)
+                    0.75 if lap_mode == "consistent" else 1.0, lapmu)
 
 
 def gamma3(u):
@@ -246,8 +247,19 @@ class OracleSim3D:
         return 2.0 * p.beta * C * (C - 1.0) * (2.0 * C - 1.0) - self.kappa_lap_C(C)
 
     def lap_mu(self, mu):
-        """Element Laplacian of mu (Sec. II.D) over the four faces."""
+        """Element Laplacian of mu.  "face" (Sec. II.D): flux through the four
+        faces, interior faces taking the mean of the two element gradients,
+        wall faces zero (eqn:bc1).  "nodal": the patch Laplacian of
+        eqn:lapl_int_mp applied to mu with the zero wall flux of eqn:bc1
+        (volume 3/4 |patch|, the lumped P1 Laplacian), averaged over the
+        element's vertices."""
         m = self.mesh
+        if self.prm.lapmu == "nodal":
+            gmu = m.grad(mu)
+            flux = np.zeros(m.N)
+            for k in range(4):
+                np.add.at(flux, m.tet[:, k], np.sum(gmu * m.nu[:, k], axis=1))
+            return (flux / (0.75 * m.patch_vol))[m.tet].mean(axis=1)
         gmu = m.grad(mu)
         out = np.zeros(m.T)
         for k in range(4):

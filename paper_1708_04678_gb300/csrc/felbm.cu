@@ -118,6 +118,10 @@ struct DevMesh {
 
 struct Phys {
     double dt, tau_l, tau_v, rho_l, rho_v, kappa, beta, mobility;
+    // element Laplacian of mu: 0 = face-averaged gradients (Sec. II.D),
+    // 1 = vertex mean of the nodal patch Laplacian, lapmu_fac * sum l_ij (mu_j - mu_i)
+    int lapmu_nodal;
+    double lapmu_fac;
     // FP32 copies, rounded once on the host
     float dt_f, dt3_f, dt2h_f, inv_tau_l_f, inv_tau_v_f, rho_v_f, drho_f, mobility_f;
 };
@@ -129,7 +133,8 @@ struct Bufs {
     double* ux;
     double* uy;
     double* mu;
-    double* gmu;     // [2][Tp]
+    double* gmu;     // [2][Tp]; FELBM_LAPMU_NODAL: the first N hold the nodal Laplacian of mu
+    double* lmu;     // alias of gmu (nodal mode)
     double* R;       // [T][18]
     double* rhs;     // [18][Np]
     double* x0;      // [18][Np] FP64 Chebyshev iterates; in the mixed solve
@@ -145,7 +150,8 @@ struct Bufs {
     float* ux32;
     float* uy32;
     float* mu32;
-    float* gmu32;    // [2][Tp]
+    float* gmu32;    // [2][Tp]; FELBM_LAPMU_NODAL: the first N hold the nodal Laplacian of mu
+    float* lmu32;    // alias of gmu32 (nodal mode)
     float* R32;      // [T][18]
     double* stage;   // [18][Np] caller-order staging
     double* diag_part; // [kDiagBlocks][kDiagSlots]
@@ -241,6 +247,17 @@ __global__ void __launch_bounds__(kBlock) k_gradmu(DevMesh m, Bufs b) {
     b.gmu[Tp + t] = gy;
 }
 
+// K3' (FELBM_LAPMU_NODAL): nodal Laplacian of mu, the patch Laplacian of C
+// applied to mu with zero wall flux (eqn:bc1), lumped P1 volume.
+__global__ void __launch_bounds__(kBlock) k_lmu(DevMesh m, Phys c, Bufs b) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m.N) return;
+    const double mi = b.mu[i];
+    double lap = 0.0;
+    for (int k = m.row_ptr[i]; k < m.row_ptr[i + 1]; ++k) lap += m.lval[k] * (b.mu[m.col[k]] - mi);
+    b.lmu[i] = c.lapmu_fac * lap;
+}
+
 // ------------------------------- K4: forces and element residual ---------
 // lap(mu)_T = (1/A) sum_{interior edges} 1/2 (grad mu_T + grad mu_T').nu_k with
 // nu_k = -2 A b_k (outward normal x length of the edge opposite vertex k);
@@ -277,12 +294,16 @@ __global__ void __launch_bounds__(128) k_element(DevMesh m, Phys c, Bufs b) {
     }
     const double third = 1.0 / 3.0;
     double Cb = Cs * third, ux = uxs * third, uy = uys * third, mub = mus * third;
-    double gmx = b.gmu[t], gmy = b.gmu[Tp + t];
     double lapmu = 0.0;
+    if (c.lapmu_nodal) {
+        lapmu = (b.lmu[v[0]] + b.lmu[v[1]] + b.lmu[v[2]]) * third;
+    } else {
+        double gmx = b.gmu[t], gmy = b.gmu[Tp + t];
 #pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        int nb = m.nbr[k * Tp + t];
-        if (nb >= 0) lapmu -= (gmx + b.gmu[nb]) * bx[k] + (gmy + b.gmu[Tp + nb]) * by[k];
+        for (int k = 0; k < 3; ++k) {
+            int nb = m.nbr[k * Tp + t];
+            if (nb >= 0) lapmu -= (gmx + b.gmu[nb]) * bx[k] + (gmy + b.gmu[Tp + nb]) * by[k];
+        }
     }
     double drho = c.rho_l - c.rho_v;
     double rhob = c.rho_v + Cb * drho;
@@ -874,7 +895,10 @@ __global__ void __launch_bounds__(kCtaThreads, 1) k_step_cta32(DevMesh m, Phys c
     const int tid = threadIdx.x, nt = blockDim.x;
     for (int i = n0 + tid; i < n1; i += nt) mu32_node(m, c, b, i);
     __syncthreads();
-    for (int t = t0 + tid; t < t1; t += nt) gradmu32_tri(m, b, t);
+    if (c.lapmu_nodal)
+        for (int i = n0 + tid; i < n1; i += nt) lmu32_node(m, c, b, i);
+    else
+        for (int t = t0 + tid; t < t1; t += nt) gradmu32_tri(m, b, t);
     __syncthreads();
     for (int t = t0 + tid; t < t1; t += nt) element32_tri(m, c, b, t);
     __syncthreads();
@@ -1027,6 +1051,7 @@ static size_t carve(const HostMesh& h, bool dev32, void* base, DevMesh* dm, Bufs
         bb.uy = cv.take<double>(Np);
         bb.mu = cv.take<double>(Np);
         bb.gmu = cv.take<double>(2 * Tp);
+        bb.lmu = bb.gmu;
         bb.R = cv.take<double>(18 * (size_t)h.T);
     } else {
         bb.dpsi = cv.take<float>(18 * Np);
@@ -1035,6 +1060,7 @@ static size_t carve(const HostMesh& h, bool dev32, void* base, DevMesh* dm, Bufs
         bb.uy32 = cv.take<float>(Np);
         bb.mu32 = cv.take<float>(Np);
         bb.gmu32 = cv.take<float>(2 * Tp);
+        bb.lmu32 = bb.gmu32;
         bb.R32 = cv.take<float>(18 * (size_t)h.T);
     }
     bb.rhs = cv.take<double>(18 * Np);
@@ -1096,9 +1122,10 @@ static int check_params(const felbm_params* p) {
         p->lap_mode < 0 || p->lap_mode > 1 || p->solver_iters < 0 || p->solver_iters == 1 ||
         p->solver_iters > 1000 || p->solver_rounds < 0 || p->solver_rounds > 20 ||
         p->solver_mode < 0 || p->solver_mode > 1 ||
-        p->n_wall_ids < 0 || p->n_wall_ids > FELBM_MAX_WALL_IDS) {
+        p->n_wall_ids < 0 || p->n_wall_ids > FELBM_MAX_WALL_IDS ||
+        (p->lapmu_mode != FELBM_LAPMU_FACE && p->lapmu_mode != FELBM_LAPMU_NODAL)) {
         set_error("felbm: invalid params (dt, tau, rho > 0; kappa, beta, mobility >= 0; lap_mode 0/1; "
-                  "solver_mode 0/1; solver_iters 0 or 2..1000; solver_rounds 0..20)");
+                  "solver_mode 0/1; solver_iters 0 or 2..1000; solver_rounds 0..20; lapmu_mode 0/1)");
         return FELBM_ERR_INVALID_ARG;
     }
     if (p->precision != FELBM_FP64 && p->precision != FELBM_FP32_DEV) {
@@ -1277,7 +1304,10 @@ static void enqueue_step(felbm_state* st, cudaStream_t s) {
         if (mt.N > 0) {
             k_mu32<<<grid_for(mt.N, kBlock), kBlock, 0, s>>>(mt, st->phys, b);
             mark(2);
-            k_gradmu32<<<grid_for(mt.T, kBlock), kBlock, 0, s>>>(mt, b);
+            if (st->phys.lapmu_nodal)
+                k_lmu32<<<grid_for(mt.N, kBlock), kBlock, 0, s>>>(mt, st->phys, b);
+            else
+                k_gradmu32<<<grid_for(mt.T, kBlock), kBlock, 0, s>>>(mt, b);
             mark(3);
             k_element32<<<grid_for(mt.T, 128), 128, 0, s>>>(mt, st->phys, b);
             mark(4);
@@ -1298,7 +1328,10 @@ static void enqueue_step(felbm_state* st, cudaStream_t s) {
     mark(1);
     k_mu<<<grid_for(m.N, kBlock), kBlock, 0, s>>>(m, st->phys, b);
     mark(2);
-    k_gradmu<<<grid_for(m.T, kBlock), kBlock, 0, s>>>(m, b);
+    if (st->phys.lapmu_nodal)
+        k_lmu<<<grid_for(m.N, kBlock), kBlock, 0, s>>>(m, st->phys, b);
+    else
+        k_gradmu<<<grid_for(m.T, kBlock), kBlock, 0, s>>>(m, b);
     mark(3);
     k_element<<<grid_for(m.T, 128), 128, 0, s>>>(m, st->phys, b);
     mark(4);
@@ -1368,6 +1401,9 @@ int felbm_init(const felbm_mesh* mesh, const felbm_params* params, const double*
     ph.kappa = params->kappa;
     ph.beta = params->beta;
     ph.mobility = params->mobility;
+    ph.lapmu_nodal = params->lapmu_mode == FELBM_LAPMU_NODAL;
+    // lval = -2 K_ij / (s |patch_i|); the lumped P1 Laplacian is -K_ij / (|patch_i| / 3)
+    ph.lapmu_fac = (params->lap_mode == FELBM_LAP_PAPER ? 1.0 : 2.0 / 3.0) * 1.5;
     ph.dt_f = (float)params->dt;
     ph.dt3_f = (float)(params->dt / 3.0);
     ph.dt2h_f = (float)(0.5 * params->dt * params->dt);
@@ -2144,6 +2180,10 @@ int felbm_adjoint_seed(felbm_state* st, const double* dL_dg, const double* dL_dh
         set_error("felbm_adjoint_seed: invalid argument");
         return FELBM_ERR_INVALID_ARG;
     }
+    if (st->phys.lapmu_nodal) {
+        set_error("felbm_adjoint_seed: the adjoint covers FELBM_LAPMU_FACE only");
+        return FELBM_ERR_UNSUPPORTED;
+    }
     if (st->dev32) {
         set_error("felbm_adjoint_seed: the adjoint is available for FELBM_FP64 states");
         return FELBM_ERR_UNSUPPORTED;
@@ -2163,6 +2203,10 @@ int felbm_adjoint_step(felbm_state* st) {
     if (!st) {
         set_error("felbm_adjoint_step: invalid argument");
         return FELBM_ERR_INVALID_ARG;
+    }
+    if (st->phys.lapmu_nodal) {
+        set_error("felbm_adjoint_step: the adjoint covers FELBM_LAPMU_FACE only");
+        return FELBM_ERR_UNSUPPORTED;
     }
     if (st->dev32) {
         set_error("felbm_adjoint_step: the adjoint is available for FELBM_FP64 states");
@@ -2195,6 +2239,10 @@ int felbm_adjoint_get(felbm_state* st, double* dL_dg, double* dL_dh, double* dL_
     if (!st || (!dL_dg != !dL_dh)) {
         set_error("felbm_adjoint_get: invalid argument");
         return FELBM_ERR_INVALID_ARG;
+    }
+    if (st->phys.lapmu_nodal) {
+        set_error("felbm_adjoint_get: the adjoint covers FELBM_LAPMU_FACE only");
+        return FELBM_ERR_UNSUPPORTED;
     }
     if (st->dev32) {
         set_error("felbm_adjoint_get: the adjoint is available for FELBM_FP64 states");

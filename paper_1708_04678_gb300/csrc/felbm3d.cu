@@ -144,6 +144,10 @@ struct DevMesh3 {
 
 struct Phys3 {
     double dt, tau_l, tau_v, rho_l, rho_v, kappa, beta, mobility;
+    // element Laplacian of mu: 0 = face-averaged gradients (Sec. II.D),
+    // 1 = vertex mean of the nodal patch Laplacian, lapmu_fac * sum l_ij (mu_j - mu_i)
+    int lapmu_nodal;
+    double lapmu_fac;
     float dt_f, dt4_f, dt2h_f, inv_tau_l_f, inv_tau_v_f, rho_v_f, drho_f, mobility_f;
 };
 
@@ -155,7 +159,8 @@ struct Bufs3 {
     double* uy;
     double* uz;
     double* mu;
-    double* gmu;     // [3][Tp]
+    double* gmu;     // [3][Tp]; FELBM_LAPMU_NODAL: the first N hold the nodal Laplacian of mu
+    double* lmu;     // alias of gmu (nodal mode)
     double* R;       // [T][38]
     double* rhs;     // [38][Np]
     double* x0;      // [38][Np] FP64 Chebyshev iterates; mixed solve: x64 and rho64
@@ -170,7 +175,8 @@ struct Bufs3 {
     float* uy32;
     float* uz32;
     float* mu32;
-    float* gmu32;    // [3][Tp]
+    float* gmu32;    // [3][Tp]; FELBM_LAPMU_NODAL: the first N hold the nodal Laplacian of mu
+    float* lmu32;    // alias of gmu32 (nodal mode)
     float* R32;      // [T][kRow]
     double* stage;   // [38][N] caller-order staging
     double* diag_part; // [kDiagBlocks][kDiagSlots]
@@ -319,6 +325,17 @@ __global__ void __launch_bounds__(kBlock) k3_gradmu(DevMesh3 m, Bufs3 b) {
     for (int a = 0; a < 3; ++a) b.gmu[a * Tp + t] = g[a];
 }
 
+// K3' (FELBM_LAPMU_NODAL): nodal Laplacian of mu, the patch Laplacian of C
+// applied to mu with zero wall flux (eqn:bc1), lumped P1 volume.
+__global__ void __launch_bounds__(kBlock) k3_lmu(DevMesh3 m, Phys3 c, Bufs3 b) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m.N) return;
+    const double mi = b.mu[i];
+    double lap = 0.0;
+    for (int k = m.row_ptr[i]; k < m.row_ptr[i + 1]; ++k) lap += m.lval[k] * (b.mu[m.col[k]] - mi);
+    b.lmu[i] = c.lapmu_fac * lap;
+}
+
 // ------------------------------- K4: forces and element residual ---------
 // lap(mu)_T = (1/V) sum_{interior faces k} 1/2 (grad mu_T + grad mu_T').nu_k
 // with nu_k = -3 V b_k (outward normal x area of the face opposite vertex
@@ -362,15 +379,20 @@ __global__ void __launch_bounds__(128) k3_element(DevMesh3 m, Phys3 c, Bufs3 b) 
         }
     }
     const double Cb = 0.25 * Cs, ux = 0.25 * uxs, uy = 0.25 * uys, uz = 0.25 * uzs, mub = 0.25 * mus;
-    const double gm[3] = {b.gmu[t], b.gmu[Tp + t], b.gmu[2 * Tp + t]};
-    double flux = 0.0;
+    double lapmu;
+    if (c.lapmu_nodal) {
+        lapmu = 0.25 * (b.lmu[v[0]] + b.lmu[v[1]] + b.lmu[v[2]] + b.lmu[v[3]]);
+    } else {
+        const double gm[3] = {b.gmu[t], b.gmu[Tp + t], b.gmu[2 * Tp + t]};
+        double flux = 0.0;
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        int nb = m.nbr[k * Tp + t];
-        if (nb >= 0)
-            flux += (gm[0] + b.gmu[nb]) * bx[k] + (gm[1] + b.gmu[Tp + nb]) * by[k] + (gm[2] + b.gmu[2 * Tp + nb]) * bz[k];
+        for (int k = 0; k < 4; ++k) {
+            int nb = m.nbr[k * Tp + t];
+            if (nb >= 0)
+                flux += (gm[0] + b.gmu[nb]) * bx[k] + (gm[1] + b.gmu[Tp + nb]) * by[k] + (gm[2] + b.gmu[2 * Tp + nb]) * bz[k];
+        }
+        lapmu = -1.5 * flux;
     }
-    const double lapmu = -1.5 * flux;
     const double drho = c.rho_l - c.rho_v;
     const double rhob = c.rho_v + Cb * drho;
     const double gr[3] = {drho * gC[0], drho * gC[1], drho * gC[2]};
@@ -873,6 +895,7 @@ static size_t carve3(const HostMesh3D& h, bool dev32, void* base, DevMesh3* dm, 
         b.uy = cv.take<double>(Np);
         b.uz = cv.take<double>(Np);
         b.gmu = cv.take<double>(3 * Tp);
+        b.lmu = b.gmu;
         b.R = cv.take<double>(38 * (size_t)std::max<int32_t>(h.T, 1));
         b.rhs = cv.take<double>(38 * Np);
         b.x0 = cv.take<double>(38 * Np);
@@ -885,6 +908,7 @@ static size_t carve3(const HostMesh3D& h, bool dev32, void* base, DevMesh3* dm, 
         b.uz32 = cv.take<float>(Np);
         b.mu32 = cv.take<float>(Np);
         b.gmu32 = cv.take<float>(3 * Tp);
+        b.lmu32 = b.gmu32;
         b.R32 = cv.take<float>((size_t)kRow * std::max<int32_t>(h.T, 1));
     }
     b.r32 = cv.take<float>((size_t)kRow * Np);
@@ -990,7 +1014,10 @@ static void enqueue_step3(felbm3d_state* st, cudaStream_t s) {
     k3_collide<<<grid_for(m.N, kBlock), kBlock, 0, s>>>(m, st->phys, b, 1);
     k3_mu<<<grid_for(m.N, kBlock), kBlock, 0, s>>>(m, st->phys, b);
     mark(1);
-    k3_gradmu<<<grid_for(m.T, kBlock), kBlock, 0, s>>>(m, b);
+    if (st->phys.lapmu_nodal)
+        k3_lmu<<<grid_for(m.N, kBlock), kBlock, 0, s>>>(m, st->phys, b);
+    else
+        k3_gradmu<<<grid_for(m.T, kBlock), kBlock, 0, s>>>(m, b);
     mark(2);
     k3_element<<<grid_for(m.T, 128), 128, 0, s>>>(m, st->phys, b);
     mark(3);
@@ -1074,7 +1101,8 @@ static int check_params3(const felbm_params* p) {
         p->n_wall_ids > FELBM_MAX_WALL_IDS || (p->lap_mode != FELBM_LAP_CONSISTENT && p->lap_mode != FELBM_LAP_PAPER) ||
         (p->precision != FELBM_FP64 && p->precision != FELBM_FP32_DEV) ||
         (p->solver_mode != FELBM_SOLVER_MIXED && p->solver_mode != FELBM_SOLVER_FP64) || p->solver_iters < 0 ||
-        p->solver_iters == 1 || p->solver_iters > 256 || p->solver_rounds < 0 || p->solver_rounds > 8) {
+        p->solver_iters == 1 || p->solver_iters > 256 || p->solver_rounds < 0 || p->solver_rounds > 8 ||
+        (p->lapmu_mode != FELBM_LAPMU_FACE && p->lapmu_mode != FELBM_LAPMU_NODAL)) {
         set_error("felbm3d_init: invalid parameters");
         return FELBM_ERR_INVALID_ARG;
     }
@@ -1144,6 +1172,9 @@ int felbm3d_init(const felbm3d_mesh* mesh, const felbm_params* params, const dou
     ph.kappa = params->kappa;
     ph.beta = params->beta;
     ph.mobility = params->mobility;
+    ph.lapmu_nodal = params->lapmu_mode == FELBM_LAPMU_NODAL;
+    // lval = -3 K_ij / (s |patch_i|); the lumped P1 Laplacian is -K_ij / (|patch_i| / 4)
+    ph.lapmu_fac = (params->lap_mode == FELBM_LAP_PAPER ? 1.0 : 0.75) * 4.0 / 3.0;
     ph.dt_f = (float)params->dt;
     ph.dt4_f = (float)(0.25 * params->dt);
     ph.dt2h_f = (float)(0.5 * params->dt * params->dt);
@@ -1507,7 +1538,10 @@ static void enqueue_step_dev32(felbm3d_state* st, cudaStream_t s) {
     const Bufs3& b = st->buf;
     k3_mu32<<<grid_for(m.N, kBlock), kBlock, 0, s>>>(m, st->phys, b);
     mark3(st, s, 1);
-    k3_gradmu32<<<grid_for(m.T, kBlock), kBlock, 0, s>>>(m, b);
+    if (st->phys.lapmu_nodal)
+        k3_lmu32<<<grid_for(m.N, kBlock), kBlock, 0, s>>>(m, st->phys, b);
+    else
+        k3_gradmu32<<<grid_for(m.T, kBlock), kBlock, 0, s>>>(m, b);
     mark3(st, s, 2);
     k3_element32<<<grid_for(m.T, kElemTets), kCoopBlock, 0, s>>>(m, st->phys, b);
     mark3(st, s, 3);

@@ -41,6 +41,17 @@ __global__ void __launch_bounds__(kBlock) k3_mu32(DevMesh3 m, Phys3 c, Bufs3 b) 
     b.mu32[i] = (float)(2.0 * c.beta * Ci * (Ci - 1.0) * (2.0 * Ci - 1.0) - (c.kappa * lap + wall * m.inv_vol[i]));
 }
 
+// FELBM_LAPMU_NODAL: nodal Laplacian of mu (patch Laplacian with zero wall
+// flux), formed in FP64 from the FP32 mu like the Laplacian of C.
+__global__ void __launch_bounds__(kBlock) k3_lmu32(DevMesh3 m, Phys3 c, Bufs3 b) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m.N) return;
+    const double mi = b.mu32[i];
+    double lap = 0.0;
+    for (int k = m.row_ptr[i]; k < m.row_ptr[i + 1]; ++k) lap += m.lval[k] * ((double)b.mu32[m.col[k]] - mi);
+    b.lmu32[i] = (float)(c.lapmu_fac * lap);
+}
+
 __global__ void __launch_bounds__(kBlock) k3_gradmu32(DevMesh3 m, Bufs3 b) {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= m.T) return;
@@ -152,13 +163,19 @@ __global__ void __launch_bounds__(kCoopBlock) k3_element32(DevMesh3 m, Phys3 c, 
             rec[EF_B1X + 3 * (n - 1) + 1][r] = by[n];
             rec[EF_B1X + 3 * (n - 1) + 2][r] = bz[n];
         }
-        const float gm0 = b.gmu32[t], gm1 = b.gmu32[Tp + t], gm2 = b.gmu32[2 * Tp + t];
-        float flux = 0.0f;
+        float lapmu;
+        if (c.lapmu_nodal) {
+            lapmu = 0.25f * (b.lmu32[v[0]] + b.lmu32[v[1]] + b.lmu32[v[2]] + b.lmu32[v[3]]);
+        } else {
+            const float gm0 = b.gmu32[t], gm1 = b.gmu32[Tp + t], gm2 = b.gmu32[2 * Tp + t];
+            float flux = 0.0f;
 #pragma unroll
-        for (int n = 0; n < 4; ++n) {
-            const int nb = m.nbr[n * Tp + t];
-            if (nb >= 0)
-                flux += (gm0 + b.gmu32[nb]) * bx[n] + (gm1 + b.gmu32[Tp + nb]) * by[n] + (gm2 + b.gmu32[2 * Tp + nb]) * bz[n];
+            for (int n = 0; n < 4; ++n) {
+                const int nb = m.nbr[n * Tp + t];
+                if (nb >= 0)
+                    flux += (gm0 + b.gmu32[nb]) * bx[n] + (gm1 + b.gmu32[Tp + nb]) * by[n] + (gm2 + b.gmu32[2 * Tp + nb]) * bz[n];
+            }
+            lapmu = -1.5f * flux;
         }
         const float drho = c.drho_f;
         const float rhob = c.rho_v_f + Cb * drho;
@@ -187,7 +204,7 @@ __global__ void __launch_bounds__(kCoopBlock) k3_element32(DevMesh3 m, Phys3 c, 
         rec[EF_UGR][r] = ubx * gr[0] + uby * gr[1] + ubz * gr[2];
         rec[EF_UGC][r] = ubx * gC[0] + uby * gC[1] + ubz * gC[2];
         rec[EF_UVH][r] = ubx * vh[0] + uby * vh[1] + ubz * vh[2];
-        rec[EF_MLAP][r] = c.mobility_f * (-1.5f * flux);
+        rec[EF_MLAP][r] = c.mobility_f * lapmu;
     }
     __syncthreads();
     // ---- phase B: directions, five lanes per tetrahedron

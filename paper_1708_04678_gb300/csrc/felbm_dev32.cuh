@@ -64,6 +64,20 @@ __device__ __forceinline__ void gradmu32_tri(const DevMesh& m, const Bufs& b, in
     b.gmu32[Tp + t] = d1 * m.grad32[3 * Tp + t] + d2 * m.grad32[5 * Tp + t];
 }
 
+// FELBM_LAPMU_NODAL: nodal Laplacian of mu (patch Laplacian with zero wall
+// flux), formed in FP64 from the FP32 mu like the Laplacian of C.
+__device__ __forceinline__ void lmu32_node(const DevMesh& m, const Phys& c, const Bufs& b, int i) {
+    const double mi = b.mu32[i];
+    double lap = 0.0;
+    for (int k = m.row_ptr[i]; k < m.row_ptr[i + 1]; ++k) lap += m.lval[k] * ((double)b.mu32[m.col[k]] - mi);
+    b.lmu32[i] = (float)(c.lapmu_fac * lap);
+}
+
+__global__ void __launch_bounds__(kBlock) k_lmu32(DevMesh m, Phys c, Bufs b) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < m.N) lmu32_node(m, c, b, i);
+}
+
 __global__ void __launch_bounds__(kBlock) k_gradmu32(DevMesh m, Bufs b) {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t < m.T) gradmu32_tri(m, b, t);
@@ -107,12 +121,16 @@ __device__ __forceinline__ void element32_tri(const DevMesh& m, const Phys& c, c
     const float gCx = dC1 * bx[1] + dC2 * bx[2], gCy = dC1 * by[1] + dC2 * by[2];
     const float dp1 = p[1] - p[0], dp2 = p[2] - p[0];
     const float gpx = dp1 * bx[1] + dp2 * bx[2], gpy = dp1 * by[1] + dp2 * by[2];
-    const float gmx = b.gmu32[t], gmy = b.gmu32[Tp + t];
     float lapmu = 0.0f;
+    if (c.lapmu_nodal) {
+        lapmu = (b.lmu32[v[0]] + b.lmu32[v[1]] + b.lmu32[v[2]]) * (1.0f / 3.0f);
+    } else {
+        const float gmx = b.gmu32[t], gmy = b.gmu32[Tp + t];
 #pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        int nb = m.nbr[k * Tp + t];
-        if (nb >= 0) lapmu -= (gmx + b.gmu32[nb]) * bx[k] + (gmy + b.gmu32[Tp + nb]) * by[k];
+        for (int k = 0; k < 3; ++k) {
+            int nb = m.nbr[k * Tp + t];
+            if (nb >= 0) lapmu -= (gmx + b.gmu32[nb]) * bx[k] + (gmy + b.gmu32[Tp + nb]) * by[k];
+        }
     }
     const float drho = c.drho_f;
     const float rhob = c.rho_v_f + Cb * drho;

@@ -19,6 +19,7 @@ MAX_WALL_IDS = 256
 LAP_CONSISTENT, LAP_PAPER = 0, 1
 FP64, FP32_DEV = 0, 1
 SOLVER_MIXED, SOLVER_FP64 = 0, 1
+LAPMU_FACE, LAPMU_NODAL = 0, 1
 
 _ERRORS = {
     -1: "invalid argument", -2: "bad mesh", -3: "CUDA error", -4: "workspace",
@@ -39,7 +40,8 @@ class Params(ctypes.Structure):
                 ("mobility", ctypes.c_double), ("phi_c", ctypes.c_double * MAX_WALL_IDS),
                 ("n_wall_ids", ctypes.c_int32), ("lap_mode", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("solver_mode", ctypes.c_int32),
-                ("solver_iters", ctypes.c_int32), ("solver_rounds", ctypes.c_int32)]
+                ("solver_iters", ctypes.c_int32), ("solver_rounds", ctypes.c_int32),
+                ("lapmu_mode", ctypes.c_int32)]
 
 
 class MeshInfo(ctypes.Structure):
@@ -173,7 +175,7 @@ def _ptr(a):
 
 
 def params_derive(phys, lap_mode=LAP_CONSISTENT, solver_iters=0, precision=FP64,
-                  solver_mode=SOLVER_MIXED, solver_rounds=0):
+                  solver_mode=SOLVER_MIXED, solver_rounds=0, lapmu_mode=LAPMU_FACE):
     """felbm_params from a physical description (sigma, xi, contact angles in
     degrees, dt, tau_l, tau_v, rho_l, rho_v, mobility)."""
     p = Params()
@@ -189,6 +191,7 @@ def params_derive(phys, lap_mode=LAP_CONSISTENT, solver_iters=0, precision=FP64,
     p.solver_mode = solver_mode
     p.solver_iters = solver_iters
     p.solver_rounds = solver_rounds
+    p.lapmu_mode = lapmu_mode
     return p
 
 

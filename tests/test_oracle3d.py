@@ -399,3 +399,37 @@ def test_contact_angle_diagnostic_of_exact_caps():
         sim = OracleSim3D(m, params_from_physical3d(_phys(xi=2.0, theta_deg=(theta, 90.0))), C0)
         d = sim.diagnostics()
         assert abs(d["theta_deg"] - theta) < 2.0, (theta, d["theta_deg"])
+
+
+def test_nodal_lapmu_is_seven_point_mean_and_has_no_growing_mode():
+    """"nodal" element Laplacian of mu: on the unjittered Kuhn mesh the mean
+    over the tetrahedron's vertices of the 7-point stencil; on a jittered
+    mesh the Cahn-Hilliard operator M11^-1 M10 lap_mu(2 beta - kappa lap)
+    has no eigenvalue with positive real part, while the paper's
+    face-averaged form has some."""
+    n = 6
+    m = _mesh(I3.kuhn_box(n, n, n, 0.0, 0, walls=False))
+    prm = params_from_physical3d(_phys(theta_deg=()), lapmu="nodal")
+    sim = OracleSim3D(m, prm, np.full(m.N, 0.5))
+    x, y, z = m.xyz.T
+    mu = np.cos(2 * np.pi * x / n) * np.sin(4 * np.pi * y / n) + 0.3 * np.cos(2 * np.pi * z / n)
+    idx = np.rint(m.xyz).astype(int) % n
+    grid = np.zeros((n, n, n))
+    grid[idx[:, 0], idx[:, 1], idx[:, 2]] = mu
+    seven = sum(np.roll(grid, s, axis=ax) for ax in range(3) for s in (1, -1)) - 6 * grid
+    node = seven[idx[:, 0], idx[:, 1], idx[:, 2]]
+    np.testing.assert_allclose(sim.lap_mu(mu), node[m.tet].mean(axis=1), atol=1e-12)
+    mj = _mesh(I3.kuhn_box(9, 9, 9, 0.15, 3, walls=False))
+    N = mj.N
+    for mode, check in (("face", lambda r: r > 1e-2), ("nodal", lambda r: r < 1e-10)):
+        p = params_from_physical3d(_phys(theta_deg=()), lapmu=mode)
+        s = OracleSim3D(mj, p, np.full(N, 0.5))
+        lapmu, lapC = np.zeros((mj.T, N)), np.zeros((N, N))
+        for j in range(N):
+            e = np.zeros(N)
+            e[j] = 1.0
+            lapmu[:, j] = s.lap_mu(e)
+            lapC[:, j] = s.kappa_lap_C(e) / p.kappa
+        A = np.linalg.solve(mj.M11.toarray(), mj.M10.toarray() @ lapmu) @ (2 * p.beta * np.eye(N) - p.kappa * lapC)
+        r = np.linalg.eigvals(A).real.max()
+        assert check(r), (mode, r)

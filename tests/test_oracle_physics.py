@@ -307,3 +307,50 @@ def test_contact_angle_of_circular_caps(theta):
     sim = OracleSim(m, params_from_physical(_params()), cap)
     d = sim.diagnostics()
     assert abs(d["theta_deg"] - theta) < 0.5
+
+
+# ------------------------------------------ element Laplacian of mu modes ---
+def _ch_operator(sim, m, prm):
+    """Nodal rate of C per unit mobility from the h-force M lap(mu) Gamma at
+    rest, linearised at C = 0: M11^-1 M10 lap_mu(2 beta C - kappa lap C)."""
+    N = m.N
+    lapmu, lapC = np.zeros((m.T, N)), np.zeros((N, N))
+    for j in range(N):
+        e = np.zeros(N)
+        e[j] = 1.0
+        lapmu[:, j] = sim.lap_mu(e)
+        lapC[:, j] = sim.kappa_lap_C(e) / prm.kappa
+    return np.linalg.solve(m.M11.toarray(), m.M10.toarray() @ lapmu) @ (2 * prm.beta * np.eye(N) - prm.kappa * lapC)
+
+
+def test_nodal_lapmu_is_five_point_mean_on_uniform_grid():
+    """"nodal" element Laplacian of mu on the unjittered grid: the mean over
+    the triangle's vertices of the 5-point stencil (walls: zero normal flux)."""
+    nx, ny = 12, 8
+    m = _mesh(I.grid_mesh(nx, ny, 0.0, 0))
+    prm = params_from_physical(_params(), lapmu="nodal")
+    sim = OracleSim(m, prm, np.full(m.N, 0.5))
+    x, y = m.xy[:, 0], m.xy[:, 1]
+    mu = np.cos(2 * np.pi * x / nx) * np.cos(0.3 * y)
+    lap = sim.lap_mu(mu)
+    node = np.zeros(m.N)
+    for j in range(1, ny):
+        for i in range(nx):
+            k = j * nx + i
+            node[k] = (mu[j * nx + (i + 1) % nx] + mu[j * nx + (i - 1) % nx]
+                       + mu[(j + 1) * nx + i] + mu[(j - 1) * nx + i] - 4 * mu[k])
+    inner = np.all((m.xy[m.tri][:, :, 1] > 0.5) & (m.xy[m.tri][:, :, 1] < ny - 0.5), axis=1)
+    np.testing.assert_allclose(lap[inner], node[m.tri[inner]].mean(axis=1), atol=1e-12)
+    assert abs(np.sum(m.area * lap)) < 1e-12 * np.sum(m.area * np.abs(lap))
+
+
+def test_face_lapmu_has_growing_modes_nodal_does_not():
+    """The paper's face-averaged element Laplacian of mu, fed to the nodes
+    through M11^-1 M10, has eigenvalues with positive real part on a
+    jittered walled mesh (an anti-diffusive Cahn-Hilliard mode: long runs
+    grow at rate M dt max Re); the "nodal" form has none."""
+    m = _mesh(I.grid_mesh(16, 8, 0.2, 0))
+    for mode, check in (("face", lambda r: r > 0.05), ("nodal", lambda r: r < 1e-10)):
+        prm = params_from_physical(_params(), lapmu=mode)
+        ev = np.linalg.eigvals(_ch_operator(OracleSim(m, prm, np.full(m.N, 0.5)), m, prm))
+        assert check(ev.real.max()), (mode, ev.real.max())
