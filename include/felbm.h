@@ -266,7 +266,10 @@ int felbm_diagnostics_groups(felbm_state* state, const felbm_diag_request* reqs,
                              felbm_diag* out);
 
 /* Copy the distributions out / in: g, h double [9][n_nodes] host, caller order.
- * Pinned host memory makes the copies asynchronous DMA.  Both synchronise. */
+ * Pinned host memory makes the copies asynchronous DMA.  get_state synchronises
+ * the stream; set_state returns once the host arrays have been read (the
+ * conversion into the state stays queued on the stream, ahead of any later
+ * work the caller enqueues there). */
 int felbm_get_state(felbm_state* state, double* g, double* h);
 int felbm_set_state(felbm_state* state, const double* g, const double* h);
 
@@ -311,8 +314,8 @@ int felbm_mass_solve(felbm_state* state, const double* B, double* X, int32_t k);
 int felbm_mass_solve_static(felbm_state* state, const double* d_B, double* d_X, int32_t k);
 
 /* ---------------------------------------------------------------- adjoint
- * Reverse-mode derivatives of felbm_step for FELBM_FP64 states (NEXT-1 of the
- * build's plan; the paper has no adjoint).  With lambda = dL/dpsi^{n+1}
+ * Reverse-mode derivatives of felbm_step for FELBM_FP64 states (the paper has
+ * no adjoint).  With lambda = dL/dpsi^{n+1}
  * seeded, felbm_adjoint_step maps it to dL/dpsi^n using the CURRENT state as
  * psi^n (restore it with felbm_checkpoint_load / felbm_set_state first) and
  * adds (d psi^{n+1}/d phi_c)^T lambda to the wetting-potential gradient.  The

@@ -102,7 +102,9 @@ int felbm3d_diagnostics(felbm3d_state* st, const felbm3d_diag_request* req, felb
 
 /* Copy the distributions to / from host arrays double [19][n_nodes] each
  * (caller order).  FP32_DEV storage converts: get returns psi^eq + dpsi, set
- * recomputes the fields and the FP32 deviations. */
+ * recomputes the fields and the FP32 deviations.  get_state synchronises the
+ * stream; set_state returns once the host arrays have been read (the
+ * conversion stays queued on the stream). */
 int felbm3d_get_state(felbm3d_state* st, double* g, double* h);
 int felbm3d_set_state(felbm3d_state* st, const double* g, const double* h);
 

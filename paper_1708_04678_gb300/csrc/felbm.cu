@@ -982,6 +982,7 @@ struct felbm_state {
     int32_t* d_cta_groups = nullptr;   // [G] in the workspace
     cudaStream_t side_stream = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    cudaEvent_t ev_copied = nullptr;   // set_state: the host arrays have been read
 };
 
 namespace felbm {
@@ -1838,12 +1839,15 @@ int felbm_set_state(felbm_state* st, const double* g, const double* h) {
     const int N = st->dm.N;
     FELBM_CUDA(cudaMemcpyAsync(st->buf.stage, g, sizeof(double) * 9 * N, cudaMemcpyHostToDevice, s));
     FELBM_CUDA(cudaMemcpyAsync(st->buf.stage + (size_t)9 * N, h, sizeof(double) * 9 * N, cudaMemcpyHostToDevice, s));
+    if (!st->ev_copied) FELBM_CUDA(cudaEventCreateWithFlags(&st->ev_copied, cudaEventDisableTiming));
+    FELBM_CUDA(cudaEventRecord(st->ev_copied, s));
     if (st->dev32)
         k_full_to_dev32<<<grid_for(N, kBlock), kBlock, 0, s>>>(st->dm, st->phys, st->buf, st->buf.stage);
     else
         k_scatter_in<<<grid_for(N, kBlock), kBlock, 0, s>>>(st->dm, st->buf.stage, st->buf.psi, 18);
     FELBM_CUDA(cudaGetLastError());
-    FELBM_CUDA(cudaStreamSynchronize(s));
+    // return once the host arrays have been read; the conversion stays queued
+    FELBM_CUDA(cudaEventSynchronize(st->ev_copied));
     return FELBM_OK;
 }
 
@@ -2274,6 +2278,7 @@ void felbm_state_destroy(felbm_state* st) {
     if (st->cap_stream) cudaStreamDestroy(st->cap_stream);
     if (st->side_stream) cudaStreamDestroy(st->side_stream);
     if (st->ev_fork) cudaEventDestroy(st->ev_fork);
+    if (st->ev_copied) cudaEventDestroy(st->ev_copied);
     if (st->ev_join) cudaEventDestroy(st->ev_join);
     for (auto& e : st->ev)
         if (e) cudaEventDestroy(e);

@@ -954,6 +954,7 @@ struct felbm3d_state {
     bool timed_step_ran = false;
     bool use_pdl = true;   // programmatic dependent launch between solve sweeps (FELBM_PDL=0: off)
     cudaEvent_t ev[6] = {};
+    cudaEvent_t ev_copied = nullptr;   // set_state: the host arrays have been read
 };
 
 namespace felbm3 {
@@ -1479,13 +1480,16 @@ int felbm3d_set_state(felbm3d_state* st, const double* g, const double* h) {
     const size_t N = st->hm.N;
     FELBM3_CUDA(cudaMemcpyAsync(st->buf.stage, g, sizeof(double) * 19 * N, cudaMemcpyDefault, s));
     FELBM3_CUDA(cudaMemcpyAsync(st->buf.stage + 19 * N, h, sizeof(double) * 19 * N, cudaMemcpyDefault, s));
+    if (!st->ev_copied) FELBM3_CUDA(cudaEventCreateWithFlags(&st->ev_copied, cudaEventDisableTiming));
+    FELBM3_CUDA(cudaEventRecord(st->ev_copied, s));
     if (st->dev32)
         k3_stage_to_dev32<<<grid_for(st->dm.N, kNodeBlock), kNodeBlock, 0, s>>>(st->dm, st->phys, st->buf);
     else
         k3_scatter_in<<<grid_for(st->dm.N, kBlock), kBlock, 0, s>>>(st->dm, st->buf.stage, st->buf.psi, 38);
     FELBM3_CUDA(cudaGetLastError());
     refresh_fields(st);
-    FELBM3_CUDA(cudaStreamSynchronize(s));
+    // return once the host arrays have been read; the conversion stays queued
+    FELBM3_CUDA(cudaEventSynchronize(st->ev_copied));
     return FELBM_OK;
 }
 
@@ -1524,6 +1528,7 @@ void felbm3d_state_destroy(felbm3d_state* st) {
     if (st->cap_stream) cudaStreamDestroy(st->cap_stream);
     for (auto& ev : st->ev)
         if (ev) cudaEventDestroy(ev);
+    if (st->ev_copied) cudaEventDestroy(st->ev_copied);
     delete st;
 }
 
