@@ -471,6 +471,12 @@ __global__ void __launch_bounds__(128) k_cheb(DevMesh m, Bufs b, const double* _
 // ~70x the FP64 rate, so only the refinement kernels pay FP64 matvecs.
 enum Final { kStore = 0, kAddPsi = 1, kAddX64 = 2, kUpdateDev = 3 };
 
+// Programmatic dependent launch: a kernel launched with the attribute may
+// start while its predecessor drains; it must wait before touching that
+// kernel's outputs.  Both are no-ops in a kernel launched without it.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_release() { asm volatile("griddepcontrol.launch_dependents;" :::); }
+
 #include "felbm_dev32.cuh"
 #include "felbm_adjoint.cuh"
 
@@ -515,8 +521,6 @@ __global__ void __launch_bounds__(128) k_cheb32(DevMesh m, Phys c, Bufs b, const
 // predecessor drains; it loads its (read-only) matrix row first and waits for
 // the predecessor's results before touching them.  Both instructions are
 // no-ops for a kernel launched without the attribute.
-__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
-__device__ __forceinline__ void pdl_release() { asm volatile("griddepcontrol.launch_dependents;" :::); }
 
 // The FP32 sweep of k_cheb32 on the ELL copy of the pattern (kW entries per
 // row, padded with the own column and value 0).  Row indices and values are
@@ -1222,7 +1226,7 @@ static void launch_sweep(felbm_state* st, const DevMesh& m, const Bufs& b, cudaS
 // bufs: the buffers the solve reads and writes (the state's own, or another
 // set of scratch buffers with the same layout).
 static const double* enqueue_solve(felbm_state* st, const DevMesh& m, const Bufs& b, cudaStream_t s,
-                                   bool into_psi) {
+                                   bool into_psi, bool after_release = false) {
     const unsigned grid = grid_for(m.N, 128);
     if (st->mode == FELBM_SOLVER_FP64) {
         const double* result = b.x1;
@@ -1244,7 +1248,8 @@ static const double* enqueue_solve(felbm_state* st, const DevMesh& m, const Bufs
         for (int k = 1; k < st->sweeps; ++k) {
             const float a = (float)st->cheb_a[k], c = (float)st->cheb_c[k];
             const bool last = r == st->rounds - 1 && k == st->sweeps - 1;
-            const bool pdl = k > 1;   // the previous launch is a sweep of this round
+            // the previous launch is a sweep of this round, or a kernel that released its dependents
+            const bool pdl = k > 1 || (k == 1 && r == 0 && after_release);
             if (!last)
                 launch_sweep<kStore>(st, m, b, s, cur, prv, a, c, k == 1, have_x64, pdl);
             else if (!into_psi)
@@ -1303,18 +1308,21 @@ static void enqueue_step(felbm_state* st, cudaStream_t s) {
         // collision is folded into the element, RHS and update kernels
         mark(1);
         if (mt.N > 0) {
+            // programmatic dependent launch along the chain when no phase
+            // events sit between the kernels
+            const bool chain = st->use_pdl && !st->timing;
             k_mu32<<<grid_for(mt.N, kBlock), kBlock, 0, s>>>(mt, st->phys, b);
             mark(2);
             if (st->phys.lapmu_nodal)
-                k_lmu32<<<grid_for(mt.N, kBlock), kBlock, 0, s>>>(mt, st->phys, b);
+                launch_k(chain, k_lmu32, dim3(grid_for(mt.N, kBlock)), dim3(kBlock), s, mt, st->phys, b);
             else
-                k_gradmu32<<<grid_for(mt.T, kBlock), kBlock, 0, s>>>(mt, b);
+                launch_k(chain, k_gradmu32, dim3(grid_for(mt.T, kBlock)), dim3(kBlock), s, mt, b);
             mark(3);
-            k_element32<<<grid_for(mt.T, 128), 128, 0, s>>>(mt, st->phys, b);
+            launch_k(chain, k_element32, dim3(grid_for(mt.T, 128)), dim3(128), s, mt, st->phys, b);
             mark(4);
-            k_rhs32<<<grid_for(mt.N, 128), 128, 0, s>>>(mt, st->phys, b, (float)st->inv_theta);
+            launch_k(chain, k_rhs32, dim3(grid_for(mt.N, 128)), dim3(128), s, mt, st->phys, b, (float)st->inv_theta);
             mark(5);
-            enqueue_solve(st, mt, st->buf, s, true);
+            enqueue_solve(st, mt, st->buf, s, true, chain);
         } else {
             mark(2);
             mark(3);

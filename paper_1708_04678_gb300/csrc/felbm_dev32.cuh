@@ -52,6 +52,7 @@ __device__ __forceinline__ void mu32_node(const DevMesh& m, const Phys& c, const
 }
 
 __global__ void __launch_bounds__(kBlock) k_mu32(DevMesh m, Phys c, Bufs b) {
+    pdl_release();
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < m.N) mu32_node(m, c, b, i);
 }
@@ -74,11 +75,15 @@ __device__ __forceinline__ void lmu32_node(const DevMesh& m, const Phys& c, cons
 }
 
 __global__ void __launch_bounds__(kBlock) k_lmu32(DevMesh m, Phys c, Bufs b) {
+    pdl_release();
+    pdl_wait();
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < m.N) lmu32_node(m, c, b, i);
 }
 
 __global__ void __launch_bounds__(kBlock) k_gradmu32(DevMesh m, Bufs b) {
+    pdl_release();
+    pdl_wait();
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t < m.T) gradmu32_tri(m, b, t);
 }
@@ -184,6 +189,8 @@ __device__ __forceinline__ void element32_tri(const DevMesh& m, const Phys& c, c
 }
 
 __global__ void __launch_bounds__(128) k_element32(DevMesh m, Phys c, Bufs b) {
+    pdl_release();
+    pdl_wait();
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t < m.T) element32_tri(m, c, b, t);
 }
@@ -258,6 +265,8 @@ __device__ __forceinline__ void rhs32_node(const DevMesh& m, const Phys& c, cons
 }
 
 __global__ void __launch_bounds__(128) k_rhs32(DevMesh m, Phys c, Bufs b, float inv_theta) {
+    pdl_release();
+    pdl_wait();
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < m.N) rhs32_node(m, c, b, i, inv_theta);
 }
