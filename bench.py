@@ -211,6 +211,21 @@ def job_rate(units_per_rank_step, steps, world, max_ms):
 
 
 # --------------------------------------------------------------- GPU arm --
+def phase_pass(st, torch, stream, flush, n):
+    """Phase split of n steps with the library's phase events switched on
+    (kept out of the timed steps: the events sit between the kernels of the
+    step graph and break its programmatic-launch chain)."""
+    st.timing_enable(True)
+    phases = []
+    for k in range(n):
+        with torch.cuda.stream(stream):
+            flush.fill_(k & 255)
+        st.step(1)
+        phases.append(st.timing_get())
+    st.timing_enable(False)
+    return phases
+
+
 def time_precision(F, torch, w, dev, precision, K, W, flush, barrier, world, dist):
     """Build a state of the workload in one precision, run W warm-up steps and
     K timed steps (L2 flushed before each), then K end-to-end steps through
@@ -241,14 +256,7 @@ def time_precision(F, torch, w, dev, precision, K, W, flush, barrier, world, dis
     barrier()
     total_ms = max_over_ranks(sum(ev0[k].elapsed_time(ev1[k]) for k in range(K)), torch, dist, world, dev)
     # phase split (and the solve sweep's launch time) from a separate pass with phase events
-    st.timing_enable(True)
-    phases = []
-    for k in range(min(K, 10)):
-        with torch.cuda.stream(stream):
-            flush.fill_(k & 255)
-        st.step(1)
-        phases.append(st.timing_get())           # synchronises the stream
-    st.timing_enable(False)
+    phases = phase_pass(st, torch, stream, flush, min(K, 10))
     diag = st.diagnostics(w["centre"], w["R"], w["phys"]["xi"])
 
     # end to end through the public API with host buffers: pinned g, h in,
@@ -356,11 +364,10 @@ def time_large(F, torch, dev, K, flush):
     mesh = F.Mesh.from_dict(w["mesh"])
     stream = torch.cuda.Stream(dev)
     st = F.State(mesh, F.params_derive(w["phys"], precision=F.FP32_DEV), w["C0"], device=dev, stream=stream)
-    st.timing_enable(True)
     tune = st.autotune(trials=2)
     for k in range(2):
         st.step(1)
-    tot, phases = 0.0, []
+    tot = 0.0
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     for k in range(K):
         with torch.cuda.stream(stream):
@@ -368,8 +375,9 @@ def time_large(F, torch, dev, K, flush):
         e0.record(stream)
         st.step(1)
         e1.record(stream)
-        phases.append(st.timing_get())
+        e1.synchronize()
         tot += e0.elapsed_time(e1)
+    phases = phase_pass(st, torch, stream, flush, min(K, 5))
     n = len(w["mesh"]["xy"])
     info = mesh.info()
     solve = statistics.mean(p["solve_ms"] for p in phases)
@@ -400,10 +408,9 @@ def time_3d(torch, dev, K, flush):
     for name, prec in (("fp32_dev", F.FP32_DEV), ("fp64", F.FP64)):
         stream = torch.cuda.Stream(dev)
         st = F3.State3D(mesh, F.params_derive(w["phys"], precision=prec), w["C0"], device=dev, stream=stream)
-        st.timing_enable(True)
         for k in range(3):
             st.step(1)
-        tot, phases = 0.0, []
+        tot = 0.0
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         for k in range(K):
             with torch.cuda.stream(stream):
@@ -411,8 +418,9 @@ def time_3d(torch, dev, K, flush):
             e0.record(stream)
             st.step(1)
             e1.record(stream)
-            phases.append(st.timing_get())
+            e1.synchronize()
             tot += e0.elapsed_time(e1)
+        phases = phase_pass(st, torch, stream, flush, min(K, 5))
         d = st.diagnostics(w["centre"], w["R"], w["phys"]["xi"], substrate=-1)
         ph = {k: statistics.mean(p[k] for p in phases) for k in phases[0]}
         r = {"ms_per_step": tot / K, "value": n * K / (tot * 1e-3), "unit": "node-updates/s",

@@ -995,7 +995,7 @@ static int solve_launches3(const felbm3d_state* st) {
 }
 static int step_launches3(const felbm3d_state* st) { return (st->dev32 ? 4 : 5) + solve_launches3(st); }
 
-static void enqueue_solve3(felbm3d_state* st, cudaStream_t s);
+static void enqueue_solve3(felbm3d_state* st, cudaStream_t s, bool after_release = false);
 static void enqueue_step_dev32(felbm3d_state* st, cudaStream_t s);
 
 // phase event k of the timed step, recorded as an external event node
@@ -1034,7 +1034,7 @@ static void enqueue_step3(felbm3d_state* st, cudaStream_t s) {
 
 // The consistent-mass solve of one step; the last sweep adds the increment
 // to psi.
-static void enqueue_solve3(felbm3d_state* st, cudaStream_t s) {
+static void enqueue_solve3(felbm3d_state* st, cudaStream_t s, bool after_release) {
     const DevMesh3& m = st->dm;
     const Bufs3& b = st->buf;
     const dim3 g2(grid_for(m.N, kNodeBlock), 2);
@@ -1056,7 +1056,8 @@ static void enqueue_solve3(felbm3d_state* st, cudaStream_t s) {
         for (int k = 1; k < st->sweeps; ++k) {
             const float a = (float)st->cheb_a[k], c = (float)st->cheb_c[k];
             const bool last = r == st->rounds - 1 && k == st->sweeps - 1;
-            const bool pdl = k > 1;   // the previous launch is a sweep of this round
+            // the previous launch is a sweep of this round, or a kernel that released its dependents
+            const bool pdl = k > 1 || (k == 1 && r == 0 && after_release);
             if (!last)
                 launch_sweep3<kStore3>(st, s, cur, prv, a, c, k == 1, have_x64, pdl);
             else if (st->dev32)
@@ -1541,18 +1542,21 @@ namespace felbm3 {
 static void enqueue_step_dev32(felbm3d_state* st, cudaStream_t s) {
     const DevMesh3& m = st->dm;
     const Bufs3& b = st->buf;
+    // programmatic dependent launch along the chain when no phase events sit
+    // between the kernels
+    const bool chain = st->use_pdl && !st->timing;
     k3_mu32<<<grid_for(m.N, kBlock), kBlock, 0, s>>>(m, st->phys, b);
     mark3(st, s, 1);
     if (st->phys.lapmu_nodal)
-        k3_lmu32<<<grid_for(m.N, kBlock), kBlock, 0, s>>>(m, st->phys, b);
+        launch3(chain, k3_lmu32, grid_for(m.N, kBlock), kBlock, s, m, st->phys, b);
     else
-        k3_gradmu32<<<grid_for(m.T, kBlock), kBlock, 0, s>>>(m, b);
+        launch3(chain, k3_gradmu32, grid_for(m.T, kBlock), kBlock, s, m, b);
     mark3(st, s, 2);
-    k3_element32<<<grid_for(m.T, kElemTets), kCoopBlock, 0, s>>>(m, st->phys, b);
+    launch3(chain, k3_element32, grid_for(m.T, kElemTets), kCoopBlock, s, m, st->phys, b);
     mark3(st, s, 3);
-    k3_rhs32<<<grid_for(m.N, kItemsPerBlock), kCoopBlock, 0, s>>>(m, st->phys, b, (float)st->inv_theta);
+    launch3(chain, k3_rhs32, grid_for(m.N, kItemsPerBlock), kCoopBlock, s, m, st->phys, b, (float)st->inv_theta);
     mark3(st, s, 4);
-    enqueue_solve3(st, s);
+    enqueue_solve3(st, s, chain);
     mark3(st, s, 5);
 }
 

@@ -31,6 +31,7 @@ __device__ __forceinline__ float dgamma32_3(int q, float dx, float dy, float dz,
 
 // ------------------------------------------------- chemical potential ------
 __global__ void __launch_bounds__(kBlock) k3_mu32(DevMesh3 m, Phys3 c, Bufs3 b) {
+    pdl_release3();
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= m.N) return;
     const double Ci = b.C[i];
@@ -44,6 +45,8 @@ __global__ void __launch_bounds__(kBlock) k3_mu32(DevMesh3 m, Phys3 c, Bufs3 b) 
 // FELBM_LAPMU_NODAL: nodal Laplacian of mu (patch Laplacian with zero wall
 // flux), formed in FP64 from the FP32 mu like the Laplacian of C.
 __global__ void __launch_bounds__(kBlock) k3_lmu32(DevMesh3 m, Phys3 c, Bufs3 b) {
+    pdl_release3();
+    pdl_wait3();
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= m.N) return;
     const double mi = b.mu32[i];
@@ -53,6 +56,8 @@ __global__ void __launch_bounds__(kBlock) k3_lmu32(DevMesh3 m, Phys3 c, Bufs3 b)
 }
 
 __global__ void __launch_bounds__(kBlock) k3_gradmu32(DevMesh3 m, Bufs3 b) {
+    pdl_release3();
+    pdl_wait3();
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= m.T) return;
     const int Tp = m.Tp;
@@ -108,6 +113,8 @@ enum ElemField {
 __global__ void __launch_bounds__(kCoopBlock) k3_element32(DevMesh3 m, Phys3 c, Bufs3 b) {
     __shared__ float rec[EF_COUNT][kElemTets];
     __shared__ int vid[4][kElemTets];
+    pdl_release3();
+    pdl_wait3();
     const int t0 = blockIdx.x * kElemTets, Tp = m.Tp;
     const int nt = min(kElemTets, m.T - t0);
     // ---- phase A: element quantities, one thread per tetrahedron
@@ -288,6 +295,8 @@ __device__ __forceinline__ float wall_diff32(const Phys3& c, const Bufs3& b, int
 }
 
 __global__ void __launch_bounds__(kCoopBlock) k3_rhs32(DevMesh3 m, Phys3 c, Bufs3 b, float inv_theta) {
+    pdl_release3();
+    pdl_wait3();
     const Coop k = coop_index(m.N);
     if (!k.active) return;
     const int i = k.item, ninc = m.ninc;
