@@ -92,6 +92,7 @@ struct DevMesh {
     int32_t ell_w;            // width of the ELL copy (max row length), 0 = none
     const int32_t* ell_col;   // [ell_w][Np] column-major ELL copy of the pattern
     const float* ell_val;     // [ell_w][Np] FP32 mass entries (padding: own column, 0)
+    const double* ell_lval;   // [ell_w][Np] patch-Laplacian coefficients of C (padding 0)
     const float* inv_lumped32;// [Np]
     const double* lumped;     // [Np]
     const double* inv_vol;    // [Np] 1 / V_i
@@ -1025,6 +1026,7 @@ static size_t carve(const HostMesh& h, bool dev32, void* base, DevMesh* dm, Bufs
     d.ell_w = ellw;
     d.ell_col = cv.take<int32_t>((size_t)std::max(ellw, 1) * Np);
     d.ell_val = cv.take<float>((size_t)std::max(ellw, 1) * Np);
+    d.ell_lval = cv.take<double>((size_t)std::max(ellw, 1) * Np);
     d.inv_lumped32 = cv.take<float>(Np);
     d.lumped = cv.take<double>(Np);
     d.inv_vol = cv.take<double>(Np);
@@ -1311,7 +1313,13 @@ static void enqueue_step(felbm_state* st, cudaStream_t s) {
             // programmatic dependent launch along the chain when no phase
             // events sit between the kernels
             const bool chain = st->use_pdl && !st->timing;
-            k_mu32<<<grid_for(mt.N, kBlock), kBlock, 0, s>>>(mt, st->phys, b);
+            switch (mt.ell_w) {
+                case 7: k_mu32<7><<<grid_for(mt.N, kBlock), kBlock, 0, s>>>(mt, st->phys, b); break;
+                case 9: k_mu32<9><<<grid_for(mt.N, kBlock), kBlock, 0, s>>>(mt, st->phys, b); break;
+                case 12: k_mu32<12><<<grid_for(mt.N, kBlock), kBlock, 0, s>>>(mt, st->phys, b); break;
+                case 16: k_mu32<16><<<grid_for(mt.N, kBlock), kBlock, 0, s>>>(mt, st->phys, b); break;
+                default: k_mu32<0><<<grid_for(mt.N, kBlock), kBlock, 0, s>>>(mt, st->phys, b);
+            }
             mark(2);
             if (st->phys.lapmu_nodal)
                 launch_k(chain, k_lmu32, dim3(grid_for(mt.N, kBlock)), dim3(kBlock), s, mt, st->phys, b);
@@ -1448,20 +1456,22 @@ int felbm_init(const felbm_mesh* mesh, const felbm_params* params, const double*
     const int ellw = st->dm.ell_w;
     std::vector<int32_t> ell_col((size_t)std::max(ellw, 1) * st->dm.Np, 0);
     std::vector<float> ell_val((size_t)std::max(ellw, 1) * st->dm.Np, 0.0f);
-    for (int32_t i = 0; i < h.N && ellw > 0; ++i) {
-        int32_t r0 = h.row_ptr[i], len = h.row_ptr[i + 1] - r0;
-        for (int k = 0; k < ellw; ++k) {
-            size_t at = (size_t)k * st->dm.Np + i;
-            ell_col[at] = k < len ? h.col[r0 + k] : i;
-            ell_val[at] = k < len ? (float)h.mass[r0 + k] : 0.0f;
-        }
-    }
+    std::vector<double> ell_lval((size_t)std::max(ellw, 1) * st->dm.Np, 0.0);
     if (const char* env = std::getenv("FELBM_PDL")) st->use_pdl = std::atoi(env) != 0;
     for (int32_t i = 0; i < h.N; ++i) {
         inv_vol[i] = 1.0 / (scale * h.patch[i]);
         inv_lumped[i] = 1.0 / h.lumped[i];
         inv_lumped32[i] = (float)inv_lumped[i];
         for (int32_t k = h.row_ptr[i]; k < h.row_ptr[i + 1]; ++k) lval[k] = -2.0 * h.stiff[k] * inv_vol[i];
+    }
+    for (int32_t i = 0; i < h.N && ellw > 0; ++i) {
+        int32_t r0 = h.row_ptr[i], len = h.row_ptr[i + 1] - r0;
+        for (int k = 0; k < ellw; ++k) {
+            size_t at = (size_t)k * st->dm.Np + i;
+            ell_col[at] = k < len ? h.col[r0 + k] : i;
+            ell_val[at] = k < len ? (float)h.mass[r0 + k] : 0.0f;
+            ell_lval[at] = k < len ? lval[r0 + k] : 0.0;
+        }
     }
     auto pad_tri = [&](const std::vector<int32_t>& src, int rows) {
         std::vector<int32_t> outv((size_t)rows * st->dm.Tp, 0);
@@ -1506,6 +1516,7 @@ int felbm_init(const felbm_mesh* mesh, const felbm_params* params, const double*
     UP(d.mval32, mval32);
     UP(d.ell_col, ell_col);
     UP(d.ell_val, ell_val);
+    UP(d.ell_lval, ell_lval);
     UP(d.inv_lumped32, inv_lumped32);
     UP(d.lumped, h.lumped);
     UP(d.inv_vol, inv_vol);
@@ -1868,7 +1879,7 @@ int felbm_get_fields(felbm_state* st, double* C, double* p, double* ux, double* 
     const DevMesh& m = st->dm;
     double* outs[5] = {C, p, ux, uy, mu};
     if (st->dev32) {
-        k_mu32<<<grid_for(m.N, kBlock), kBlock, 0, s>>>(m, st->phys, st->buf);
+        k_mu32<0><<<grid_for(m.N, kBlock), kBlock, 0, s>>>(m, st->phys, st->buf);
         FELBM_CUDA(cudaGetLastError());
         const float* srcs[5] = {nullptr, st->buf.p32, st->buf.ux32, st->buf.uy32, st->buf.mu32};
         for (int k = 0; k < 5; ++k) {

@@ -51,10 +51,38 @@ __device__ __forceinline__ void mu32_node(const DevMesh& m, const Phys& c, const
     b.mu32[i] = (float)(2.0 * c.beta * Ci * (Ci - 1.0) * (2.0 * Ci - 1.0) - (c.kappa * lap + wall * m.inv_vol[i]));
 }
 
+// kW > 0: the same sum over the ELL copy of the row (same order, zero
+// padding), its columns and coefficients loaded up front so the gathers of
+// C are issued together; kW = 0: CSR.
+template <int kW>
 __global__ void __launch_bounds__(kBlock) k_mu32(DevMesh m, Phys c, Bufs b) {
     pdl_release();
     int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < m.N) mu32_node(m, c, b, i);
+    if (i >= m.N) return;
+    if constexpr (kW == 0) {
+        mu32_node(m, c, b, i);
+    } else {
+        const int Np = m.Np;
+        int col[kW];
+        double l[kW];
+#pragma unroll
+        for (int k = 0; k < kW; ++k) {
+            col[k] = m.ell_col[k * Np + i];
+            l[k] = m.ell_lval[k * Np + i];
+        }
+        const double Ci = b.C[i];
+        double lap = 0.0;
+#pragma unroll
+        for (int k = 0; k < kW; ++k) lap += l[k] * (b.C[col[k]] - Ci);
+        double wall = 0.0;
+        for (int k = m.winc_ptr[i]; k < m.winc_ptr[i + 1]; ++k) {
+            int e = m.winc_edge[k];
+            double Ca = b.C[m.wall_a[e]], Cb = b.C[m.wall_b[e]];
+            double s = 0.5 * (Ca + Cb) - (Ca * Ca + Ca * Cb + Cb * Cb) * (1.0 / 3.0);
+            wall -= m.wall_phi[e] * m.wall_len[e] * s;
+        }
+        b.mu32[i] = (float)(2.0 * c.beta * Ci * (Ci - 1.0) * (2.0 * Ci - 1.0) - (c.kappa * lap + wall * m.inv_vol[i]));
+    }
 }
 
 __device__ __forceinline__ void gradmu32_tri(const DevMesh& m, const Bufs& b, int t) {
