@@ -93,6 +93,10 @@ struct DevMesh {
     const int32_t* ell_col;   // [ell_w][Np] column-major ELL copy of the pattern
     const float* ell_val;     // [ell_w][Np] FP32 mass entries (padding: own column, 0)
     const double* ell_lval;   // [ell_w][Np] patch-Laplacian coefficients of C (padding 0)
+    int32_t iell_w;           // width of the ELL copy of node -> triangle incidence, 0 = none
+    const int32_t* iell_tri;  // [iell_w][Np] incident triangle (padding: T, a zero residual row)
+    const float* iell_bx32;   // [iell_w][Np] the node's shape gradient in that triangle
+    const float* iell_by32;
     const float* inv_lumped32;// [Np]
     const double* lumped;     // [Np]
     const double* inv_vol;    // [Np] 1 / V_i
@@ -1001,6 +1005,16 @@ static int ell_width(const HostMesh& h) {
     return 0;
 }
 
+// Width of the incidence ELL used by the FP32 RHS gather: the most triangles
+// at one node rounded up to a compiled width; 0 (CSR) beyond 12.
+static int inc_width(const HostMesh& h) {
+    int w = 0;
+    for (int32_t i = 0; i < h.N; ++i) w = std::max(w, h.inc_ptr[i + 1] - h.inc_ptr[i]);
+    for (int c : {6, 8, 12})
+        if (w <= c) return c;
+    return 0;
+}
+
 // Layout of the workspace; with base == nullptr only the size is computed.
 static size_t carve(const HostMesh& h, bool dev32, void* base, DevMesh* dm, Bufs* b,
                     GroupTables* gtab = nullptr, AdjBufs* adj = nullptr) {
@@ -1027,6 +1041,11 @@ static size_t carve(const HostMesh& h, bool dev32, void* base, DevMesh* dm, Bufs
     d.ell_col = cv.take<int32_t>((size_t)std::max(ellw, 1) * Np);
     d.ell_val = cv.take<float>((size_t)std::max(ellw, 1) * Np);
     d.ell_lval = cv.take<double>((size_t)std::max(ellw, 1) * Np);
+    const int iw = inc_width(h);
+    d.iell_w = iw;
+    d.iell_tri = cv.take<int32_t>((size_t)std::max(iw, 1) * Np);
+    d.iell_bx32 = cv.take<float>((size_t)std::max(iw, 1) * Np);
+    d.iell_by32 = cv.take<float>((size_t)std::max(iw, 1) * Np);
     d.inv_lumped32 = cv.take<float>(Np);
     d.lumped = cv.take<double>(Np);
     d.inv_vol = cv.take<double>(Np);
@@ -1068,7 +1087,7 @@ static size_t carve(const HostMesh& h, bool dev32, void* base, DevMesh* dm, Bufs
         bb.mu32 = cv.take<float>(Np);
         bb.gmu32 = cv.take<float>(2 * Tp);
         bb.lmu32 = bb.gmu32;
-        bb.R32 = cv.take<float>(18 * (size_t)h.T);
+        bb.R32 = cv.take<float>(18 * ((size_t)h.T + 1));   // row T: zeros (incidence padding)
     }
     bb.rhs = cv.take<double>(18 * Np);
     bb.x0 = cv.take<double>(18 * Np);
@@ -1328,7 +1347,12 @@ static void enqueue_step(felbm_state* st, cudaStream_t s) {
             mark(3);
             launch_k(chain, k_element32, dim3(grid_for(mt.T, 128)), dim3(128), s, mt, st->phys, b);
             mark(4);
-            launch_k(chain, k_rhs32, dim3(grid_for(mt.N, 128)), dim3(128), s, mt, st->phys, b, (float)st->inv_theta);
+            switch (mt.iell_w) {
+                case 6: launch_k(chain, k_rhs32<6>, dim3(grid_for(mt.N, 128)), dim3(128), s, mt, st->phys, b, (float)st->inv_theta); break;
+                case 8: launch_k(chain, k_rhs32<8>, dim3(grid_for(mt.N, 128)), dim3(128), s, mt, st->phys, b, (float)st->inv_theta); break;
+                case 12: launch_k(chain, k_rhs32<12>, dim3(grid_for(mt.N, 128)), dim3(128), s, mt, st->phys, b, (float)st->inv_theta); break;
+                default: launch_k(chain, k_rhs32<0>, dim3(grid_for(mt.N, 128)), dim3(128), s, mt, st->phys, b, (float)st->inv_theta);
+            }
             mark(5);
             enqueue_solve(st, mt, st->buf, s, true, chain);
         } else {
@@ -1526,6 +1550,23 @@ int felbm_init(const felbm_mesh* mesh, const felbm_params* params, const double*
     UP(d.inc_by, h.inc_by);
     UP(d.inc_bx32, inc_bx32);
     UP(d.inc_by32, inc_by32);
+    {
+        const int iw = st->dm.iell_w;
+        const size_t Npi = st->dm.Np;
+        std::vector<int32_t> itri((size_t)std::max(iw, 1) * Npi, h.T);
+        std::vector<float> ibx((size_t)std::max(iw, 1) * Npi, 0.0f), iby(ibx.size(), 0.0f);
+        for (int32_t i = 0; i < h.N && iw > 0; ++i)
+            for (int32_t k = h.inc_ptr[i]; k < h.inc_ptr[i + 1]; ++k) {
+                const size_t at = (size_t)(k - h.inc_ptr[i]) * Npi + i;
+                itri[at] = h.inc_tri[k];
+                ibx[at] = inc_bx32[k];
+                iby[at] = inc_by32[k];
+            }
+        UP(d.iell_tri, itri);
+        UP(d.iell_bx32, ibx);
+        UP(d.iell_by32, iby);
+        if (dev32 && e == cudaSuccess) e = cudaMemsetAsync(st->buf.R32 + (size_t)18 * h.T, 0, 18 * sizeof(float), s);
+    }
     UP(d.wall_a, h.wall_a);
     UP(d.wall_b, h.wall_b);
     UP(d.wall_id, h.wall_id);

@@ -227,15 +227,40 @@ __global__ void __launch_bounds__(128) k_element32(DevMesh m, Phys c, Bufs b) {
 // As k_rhs; the wall term needs psi_hat_opp - psi_hat at a node, which in the
 // split form is  g: -2 w rho (e.u) + (1-omega)(dg_opp - dg),
 //                h: -6 w C (e.u)   + (1-omega)(dh_opp - dh).
+// kI > 0: the incident triangles from the incidence ELL (padding: the zero
+// residual row T), their ids and gradients loaded up front; kI = 0: CSR.
+template <int kI = 0>
 __device__ __forceinline__ void rhs32_node(const DevMesh& m, const Phys& c, const Bufs& b, int i, float inv_theta) {
     const int Np = m.Np;
     float acc[18];
 #pragma unroll
     for (int q = 0; q < 18; ++q) acc[q] = 0.0f;
     const float c1 = c.dt3_f, c2 = c.dt2h_f;
-    for (int k = m.inc_ptr[i]; k < m.inc_ptr[i + 1]; ++k) {
-        int t = m.inc_tri[k];
-        float bxi = m.inc_bx32[k], byi = m.inc_by32[k];
+    constexpr int kIr = kI > 0 ? kI : 1;
+    int tt[kIr];
+    float bxx[kIr], byy[kIr];
+    if constexpr (kI > 0) {
+#pragma unroll
+        for (int k = 0; k < kI; ++k) {
+            tt[k] = m.iell_tri[k * Np + i];
+            bxx[k] = m.iell_bx32[k * Np + i];
+            byy[k] = m.iell_by32[k * Np + i];
+        }
+    }
+    const int k0 = kI > 0 ? 0 : m.inc_ptr[i], k1 = kI > 0 ? kI : m.inc_ptr[i + 1];
+#pragma unroll(kI > 0 ? kIr : 1)
+    for (int k = k0; k < k1; ++k) {
+        int t;
+        float bxi, byi;
+        if constexpr (kI > 0) {
+            t = tt[k];
+            bxi = bxx[k];
+            byi = byy[k];
+        } else {
+            t = m.inc_tri[k];
+            bxi = m.inc_bx32[k];
+            byi = m.inc_by32[k];
+        }
         const float2* src = reinterpret_cast<const float2*>(b.R32 + (size_t)t * 18);
         float r[18];
 #pragma unroll
@@ -292,11 +317,12 @@ __device__ __forceinline__ void rhs32_node(const DevMesh& m, const Phys& c, cons
     }
 }
 
+template <int kI>
 __global__ void __launch_bounds__(128) k_rhs32(DevMesh m, Phys c, Bufs b, float inv_theta) {
     pdl_release();
     pdl_wait();
     int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < m.N) rhs32_node(m, c, b, i, inv_theta);
+    if (i < m.N) rhs32_node<kI>(m, c, b, i, inv_theta);
 }
 
 // ---------------------------- update of fields and deviations (node) ------
