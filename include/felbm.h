@@ -239,6 +239,14 @@ int felbm_diagnostics(felbm_state* state, const felbm_diag_request* req, felbm_d
  * is rebuilt at the next felbm_step.  Results do not depend on the schedule. */
 int felbm_batch_schedule(felbm_state* state, int32_t cta_max_nodes);
 
+/* Threads per node of the FP32 solve sweeps (states with an FP32 solve):
+ * 1, 2, 3 or 6, each owning 18 / parts of the node's right-hand sides.  Every
+ * choice performs the same arithmetic per row, so the trajectory does not
+ * depend on it; felbm_autotune picks one by timing.  Default 2.  The step
+ * graph is rebuilt at the next felbm_step.  FELBM_ERR_INVALID_ARG for any
+ * other value. */
+int felbm_sweep_parts(felbm_state* state, int32_t parts);
+
 typedef struct felbm_tune_result {
     int32_t sweep_parts;     /* chosen threads per node of the FP32 solve sweeps */
     float parts_ms[4];       /* step time with 1, 2, 3, 6 threads per node (0 = not timed) */
@@ -250,7 +258,8 @@ typedef struct felbm_tune_result {
 
 /* Autotuner: times `trials` steps (after one warm-up step) per candidate and
  * keeps the fastest -- first the threads per node of the FP32 solve sweeps
- * (1, 2, 3 or 6; states with an FP32 solve and an ELL pattern), then, for
+ * (1, 2, 3 or 6; states with an FP32 solve and an ELL pattern; see
+ * felbm_sweep_parts), then, for
  * FP32_DEV batches, each distinct split of the members (tiled only, CTA per
  * member up to 2^11 .. 2^17 nodes).  The state and the step count are saved
  * before and restored after, so the simulation is unchanged.  Synchronises. */

@@ -2070,6 +2070,17 @@ int felbm_batch_schedule(felbm_state* st, int32_t cta_max_nodes) {
     return FELBM_OK;
 }
 
+int felbm_sweep_parts(felbm_state* st, int32_t parts) {
+    if (!st || !(parts == 1 || parts == 2 || parts == 3 || parts == 6)) {
+        set_error("felbm_sweep_parts: invalid argument (1, 2, 3 or 6)");
+        return FELBM_ERR_INVALID_ARG;
+    }
+    FELBM_CUDA(cudaStreamSynchronize(st->stream));
+    st->sweep_parts = parts;
+    drop_graph(st);
+    return FELBM_OK;
+}
+
 }  // extern "C"
 
 

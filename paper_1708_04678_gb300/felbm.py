@@ -134,6 +134,7 @@ def _declare(lib):
         "felbm_checkpoint_save": (ctypes.c_int, [_P, _P]),
         "felbm_checkpoint_load": (ctypes.c_int, [_P, _P]),
         "felbm_batch_schedule": (ctypes.c_int, [_P, _I32]),
+        "felbm_sweep_parts": (ctypes.c_int, [_P, _I32]),
         "felbm_autotune": (ctypes.c_int, [_P, _I32, ctypes.POINTER(TuneResult)]),
         "felbm_timing_enable": (ctypes.c_int, [_P, _I32]),
         "felbm_timing_get": (ctypes.c_int, [_P, ctypes.POINTER(StepTiming)]),
@@ -401,6 +402,9 @@ class State:
 
     def batch_schedule(self, cta_max_nodes):
         _check(lib().felbm_batch_schedule(self.handle, int(cta_max_nodes)))
+
+    def sweep_parts(self, parts):
+        _check(lib().felbm_sweep_parts(self.handle, int(parts)))
 
     def autotune(self, trials=5):
         r = TuneResult()

@@ -130,6 +130,48 @@ def test_autotuned_sweep_split_gives_identical_steps():
     np.testing.assert_array_equal(ha, hb)
 
 
+SWEEP_CASES = {
+    "free40": lambda: I.small_free_droplet(n=40, R=9.0, seed=5),
+    "sessile": lambda: I.small_sessile(nx=40, ny=20, R=9.0, theta=60.0),
+}
+
+
+@pytest.mark.parametrize("case,parts", [("free40", 1), ("free40", 3), ("free40", 6), ("sessile", 3)])
+def test_sweep_layouts_give_identical_steps(case, parts):
+    """Every split of a node's right-hand sides over threads gives the same
+    bits as the default two threads per node, on meshes of many thread
+    blocks with a ragged tail; switching mid-run is allowed."""
+    w = SWEEP_CASES[case]()
+    a = _dev(w)
+    b = _dev(w)
+    a.sweep_parts(2)
+    b.sweep_parts(parts)
+    a.step(12)
+    b.step(12)
+    ga, ha = a.get_state()
+    gb, hb = b.get_state()
+    np.testing.assert_array_equal(ga, gb)
+    np.testing.assert_array_equal(ha, hb)
+    b.sweep_parts(2)
+    a.sweep_parts(parts)
+    a.step(4)
+    b.step(4)
+    ga, ha = a.get_state()
+    gb, hb = b.get_state()
+    np.testing.assert_array_equal(ga, gb)
+    np.testing.assert_array_equal(ha, hb)
+    assert a.diagnostics(w["centre"], w["R"], 4.0)["status"] == 0
+    assert np.isfinite(ga).all() and np.abs(ga).max() > 0
+
+
+def test_sweep_parts_rejects_bad_values():
+    w = I.small_free_droplet(n=16, R=4.0)
+    b = _dev(w)
+    for bad in (0, 4, 5, 7, -1):
+        with pytest.raises(F.FelbmError):
+            b.sweep_parts(bad)
+
+
 def test_free_droplet_256_fp32_full_size_against_oracle():
     """The benchmark's workload and launch configuration (autotuned sweep
     split) for three steps against the FP64 oracle, at FP32 level."""
