@@ -231,6 +231,23 @@ int felbm_step(felbm_state* state, int32_t n_steps);
  * the state holds a NaN or Inf. */
 int felbm_diagnostics(felbm_state* state, const felbm_diag_request* req, felbm_diag* out);
 
+/* Raw sums behind one felbm_diag and the step they belong to (doubles). */
+#define FELBM_DIAG_SLOTS 16
+
+/* felbm_diagnostics in two halves, so that reading one step's result back
+ * does not hold up the host.  felbm_diagnostics_enqueue queues the same
+ * device reductions on the state's stream, then an asynchronous copy of their
+ * raw sums into `slots` (FELBM_DIAG_SLOTS doubles of host memory,
+ * caller-owned; pinned for the copy to be asynchronous), writes the current
+ * step count into the last slot, and returns without synchronising.  Once
+ * the stream has passed that point (the caller synchronised the stream or an
+ * event recorded after it, or called a synchronising function of the
+ * library), felbm_diag_finish turns the sums into *out exactly as
+ * felbm_diagnostics does (same req), returning FELBM_ERR_NONFINITE with *out
+ * filled if the state held a NaN or Inf.  Neither allocates. */
+int felbm_diagnostics_enqueue(felbm_state* state, const felbm_diag_request* req, double* slots);
+int felbm_diag_finish(felbm_state* state, const felbm_diag_request* req, const double* slots, felbm_diag* out);
+
 /* Batch schedule (FELBM_FP32_DEV states): members (groups) of at most
  * cta_max_nodes nodes each run in ONE thread block that performs the whole
  * time step with block-level barriers only (no kernel boundaries), on a side
@@ -276,9 +293,11 @@ int felbm_diagnostics_groups(felbm_state* state, const felbm_diag_request* reqs,
 
 /* Copy the distributions out / in: g, h double [9][n_nodes] host, caller order.
  * Pinned host memory makes the copies asynchronous DMA.  get_state synchronises
- * the stream; set_state returns once the host arrays have been read (the
- * conversion into the state stays queued on the stream, ahead of any later
- * work the caller enqueues there). */
+ * the stream.  set_state copies on a stream of its own into one of two input
+ * buffers used in turn, so the copy overlaps the work already queued on the
+ * state's stream (the previous step); it returns once the host arrays have
+ * been read, and the conversion into the state stays queued on the state's
+ * stream behind that work, ahead of any later work the caller enqueues there. */
 int felbm_get_state(felbm_state* state, double* g, double* h);
 int felbm_set_state(felbm_state* state, const double* g, const double* h);
 

@@ -159,14 +159,18 @@ struct Bufs {
     float* lmu32;    // alias of gmu32 (nodal mode)
     float* R32;      // [T][18]
     double* stage;   // [18][Np] caller-order staging
+    double* in0;     // [18][Np] two caller-order input buffers of felbm_set_state, used in
+    double* in1;     //          turn so a copy can run while the previous input converts
     double* diag_part; // [kDiagBlocks][kDiagSlots]
     double* diag_out;  // [kDiagSlots]
     double* Cdiag;     // [Np]
 };
 
 constexpr int kBlock = 256;
-constexpr int kDiagBlocks = 304;   // fixed grid (2 x 152 SMs): the reduction order never changes
+constexpr int kDiagBlocks = 608;   // fixed grid (4 x 152 SMs): the reduction order never changes
 constexpr int kDiagSlots = 16;
+constexpr int kDiagSums = 13;        // slots filled by k_diag_final
+constexpr int kDiagStepSlot = 15;    // felbm_diagnostics_enqueue: the step count
 
 // ------------------------------------------------------ K1: collision -----
 // Moments of the pre-collision state (C = sum h, p = sum g, rho u = sum e g /
@@ -672,25 +676,31 @@ __device__ __forceinline__ double min_image(double d, double L) {
     return L > 0.0 ? d - L * rint(d / L) : d;
 }
 
+// Block reduction of NS sums and NM maxima to out[0 .. NS+NM), in a fixed
+// order.  FP64 adds run at 1/64 of the FP32 rate on this part, so every
+// value is added once: the threads' partials go to shared memory, NV x NW
+// threads each combine one interleaved segment of 32, and NV threads combine
+// the NW segments (a warp-shuffle tree in every lane would add each value
+// five times over).
 template <int NS, int NM>
 __device__ void block_reduce_store(double (&s)[NS], double (&mx)[NM], double* out) {
-    __shared__ double sh[kBlock / 32][NS + NM];
-    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    constexpr int NV = NS + NM, NW = kBlock / 32, L = kBlock + 2;
+    __shared__ double sh[NV][L];
+    __shared__ double part[NV][NW];
 #pragma unroll
-    for (int k = 0; k < NS; ++k) s[k] = warp_sum(s[k]);
-#pragma unroll
-    for (int k = 0; k < NM; ++k) mx[k] = warp_max(mx[k]);
-    if (lane == 0) {
-#pragma unroll
-        for (int k = 0; k < NS; ++k) sh[wid][k] = s[k];
-#pragma unroll
-        for (int k = 0; k < NM; ++k) sh[wid][NS + k] = mx[k];
+    for (int k = 0; k < NV; ++k) sh[k][threadIdx.x] = k < NS ? s[k] : mx[k - NS];
+    __syncthreads();
+    if (threadIdx.x < NV * NW) {
+        const int k = threadIdx.x / NW, seg = threadIdx.x - k * NW;
+        double r = sh[k][seg];
+        for (int j = 1; j < 32; ++j) r = k < NS ? r + sh[k][seg + NW * j] : fmax(r, sh[k][seg + NW * j]);
+        part[k][seg] = r;
     }
     __syncthreads();
-    if (threadIdx.x < NS + NM) {
-        int k = threadIdx.x;
-        double r = sh[0][k];
-        for (int w = 1; w < kBlock / 32; ++w) r = k < NS ? r + sh[w][k] : fmax(r, sh[w][k]);
+    if (threadIdx.x < NV) {
+        const int k = threadIdx.x;
+        double r = part[k][0];
+        for (int w = 1; w < NW; ++w) r = k < NS ? r + part[k][w] : fmax(r, part[k][w]);
         out[k] = r;
     }
 }
@@ -834,13 +844,19 @@ __global__ void __launch_bounds__(kBlock) k_diag_groups(DevMesh m, Phys c, Bufs 
 // fixed shuffle tree -- the same order on every call.
 __global__ void k_diag_final(Bufs b) {
     int k = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (k >= 13) return;
+    if (k >= kDiagSums) return;
     bool is_max = (k == 10 || k == 12);
     double r = is_max ? -1e300 : 0.0;
-    for (int blk = lane; blk < kDiagBlocks; blk += 32) {
-        double v = b.diag_part[(size_t)blk * kDiagSlots + k];
-        r = is_max ? fmax(r, v) : r + v;
+    // every lane's partials loaded before they are combined (in block order)
+    constexpr int kPer = (kDiagBlocks + 31) / 32;
+    double v[kPer];
+#pragma unroll
+    for (int j = 0; j < kPer; ++j) {
+        const int blk = lane + 32 * j;
+        v[j] = blk < kDiagBlocks ? b.diag_part[(size_t)blk * kDiagSlots + k] : (is_max ? -1e300 : 0.0);
     }
+#pragma unroll
+    for (int j = 0; j < kPer; ++j) r = is_max ? fmax(r, v[j]) : r + v[j];
     r = is_max ? warp_max(r) : warp_sum(r);
     if (lane == 0) b.diag_out[k] = r;
 }
@@ -992,6 +1008,9 @@ struct felbm_state {
     cudaStream_t side_stream = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     cudaEvent_t ev_copied = nullptr;   // set_state: the host arrays have been read
+    cudaStream_t copy_stream = nullptr;     // set_state's host-to-device copies
+    cudaEvent_t ev_in_free[2] = {};         // the conversion that last read buf.in0 / in1 has run
+    int in_next = 0;                        // input buffer of the next set_state
 };
 
 namespace felbm {
@@ -1098,6 +1117,8 @@ static size_t carve(const HostMesh& h, bool dev32, void* base, DevMesh* dm, Bufs
     bb.e0 = cv.take<float>(18 * Np);
     bb.e1 = cv.take<float>(18 * Np);
     bb.stage = cv.take<double>(18 * Np);
+    bb.in0 = cv.take<double>(18 * Np);
+    bb.in1 = cv.take<double>(18 * Np);
     bb.diag_part = cv.take<double>((size_t)kDiagBlocks * kDiagSlots);
     bb.diag_out = cv.take<double>(kDiagSlots);
     bb.Cdiag = cv.take<double>(Np);
@@ -1765,10 +1786,10 @@ static DiagReq make_req(const felbm_state* st, const felbm_diag_request* req) {
 // felbm_diag from the reduced slots; the contact angle uses the mean height
 // of the substrate wall nodes among the given wall edges.
 static felbm_diag fill_diag(const felbm_state* st, const double* v, double mass0, int64_t nodes, int substrate,
-                            const int32_t* edges, int32_t n_edges) {
+                            const int32_t* edges, int32_t n_edges, int64_t step) {
     const HostMesh& h = st->hm;
     felbm_diag d{};
-    d.step = st->step;
+    d.step = step;
     d.mass = v[0];
     d.mass0 = mass0;
     d.mass_drift_rel = mass0 != 0.0 ? (v[0] - mass0) / mass0 : 0.0;
@@ -1827,9 +1848,45 @@ int felbm_diagnostics(felbm_state* st, const felbm_diag_request* req, felbm_diag
     double v[kDiagSlots];
     FELBM_CUDA(cudaMemcpyAsync(v, st->buf.diag_out, sizeof v, cudaMemcpyDeviceToHost, s));
     FELBM_CUDA(cudaStreamSynchronize(s));
-    *out = fill_diag(st, v, st->mass0, st->hm.N, rq.substrate, nullptr, st->hm.E);
+    *out = fill_diag(st, v, st->mass0, st->hm.N, rq.substrate, nullptr, st->hm.E, st->step);
     if (out->status != FELBM_OK) {
         set_error("felbm_diagnostics: non-finite values in the state");
+        return FELBM_ERR_NONFINITE;
+    }
+    return FELBM_OK;
+}
+
+int felbm_diagnostics_enqueue(felbm_state* st, const felbm_diag_request* req, double* slots) {
+    if (!st || !slots) {
+        set_error("felbm_diagnostics_enqueue: invalid argument");
+        return FELBM_ERR_INVALID_ARG;
+    }
+    static_assert(kDiagSlots == FELBM_DIAG_SLOTS, "raw diagnostic sums");
+    DiagReq rq = make_req(st, req);
+    cudaStream_t s = st->stream;
+    if (st->dev32)
+        k_diag_nodes<true><<<kDiagBlocks, kBlock, 0, s>>>(st->dm, st->phys, st->buf, rq);
+    else
+        k_diag_nodes<false><<<kDiagBlocks, kBlock, 0, s>>>(st->dm, st->phys, st->buf, rq);
+    k_diag_edges<<<kDiagBlocks, kBlock, 0, s>>>(st->dm, st->buf, rq);
+    k_diag_final<<<1, 13 * 32, 0, s>>>(st->buf);
+    FELBM_CUDA(cudaGetLastError());
+    // the reduced sums arrive asynchronously; the step count is the host's now
+    FELBM_CUDA(cudaMemcpyAsync(slots, st->buf.diag_out, sizeof(double) * kDiagSums, cudaMemcpyDeviceToHost, s));
+    slots[kDiagStepSlot] = (double)st->step;
+    return FELBM_OK;
+}
+
+int felbm_diag_finish(felbm_state* st, const felbm_diag_request* req, const double* slots, felbm_diag* out) {
+    if (!st || !slots || !out) {
+        set_error("felbm_diag_finish: invalid argument");
+        return FELBM_ERR_INVALID_ARG;
+    }
+    const DiagReq rq = make_req(st, req);
+    *out = fill_diag(st, slots, st->mass0, st->hm.N, rq.substrate, nullptr, st->hm.E,
+                     (int64_t)slots[kDiagStepSlot]);
+    if (out->status != FELBM_OK) {
+        set_error("felbm_diag_finish: non-finite values in the state");
         return FELBM_ERR_NONFINITE;
     }
     return FELBM_OK;
@@ -1862,7 +1919,7 @@ int felbm_diagnostics_groups(felbm_state* st, const felbm_diag_request* reqs, in
         const double* vg = v.data() + (size_t)g * kDiagSlots;
         double m0 = g < (int32_t)st->gmass0.size() ? st->gmass0[g] : vg[0];
         out[g] = fill_diag(st, vg, m0, h.grp_size[g], rq[g].substrate, h.grp_wall_edge.data() + h.grp_wall_ptr[g],
-                           h.grp_wall_ptr[g + 1] - h.grp_wall_ptr[g]);
+                           h.grp_wall_ptr[g + 1] - h.grp_wall_ptr[g], st->step);
         bad = bad || out[g].status != FELBM_OK;
     }
     if (bad) {
@@ -1897,15 +1954,28 @@ int felbm_set_state(felbm_state* st, const double* g, const double* h) {
     }
     cudaStream_t s = st->stream;
     const int N = st->dm.N;
-    FELBM_CUDA(cudaMemcpyAsync(st->buf.stage, g, sizeof(double) * 9 * N, cudaMemcpyHostToDevice, s));
-    FELBM_CUDA(cudaMemcpyAsync(st->buf.stage + (size_t)9 * N, h, sizeof(double) * 9 * N, cudaMemcpyHostToDevice, s));
+    if (!st->copy_stream) FELBM_CUDA(cudaStreamCreateWithFlags(&st->copy_stream, cudaStreamNonBlocking));
     if (!st->ev_copied) FELBM_CUDA(cudaEventCreateWithFlags(&st->ev_copied, cudaEventDisableTiming));
-    FELBM_CUDA(cudaEventRecord(st->ev_copied, s));
+    for (auto& ev : st->ev_in_free)
+        if (!ev) FELBM_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    // The copy runs on its own stream into the input buffer not used by the
+    // previous call, so it overlaps whatever the state's stream is running
+    // (the previous step); it waits only for the conversion that last read
+    // this buffer.  The conversion waits for the copy on the state's stream.
+    const int k = st->in_next;
+    st->in_next ^= 1;
+    double* in = k ? st->buf.in1 : st->buf.in0;
+    FELBM_CUDA(cudaStreamWaitEvent(st->copy_stream, st->ev_in_free[k], 0));
+    FELBM_CUDA(cudaMemcpyAsync(in, g, sizeof(double) * 9 * N, cudaMemcpyHostToDevice, st->copy_stream));
+    FELBM_CUDA(cudaMemcpyAsync(in + (size_t)9 * N, h, sizeof(double) * 9 * N, cudaMemcpyHostToDevice, st->copy_stream));
+    FELBM_CUDA(cudaEventRecord(st->ev_copied, st->copy_stream));
+    FELBM_CUDA(cudaStreamWaitEvent(s, st->ev_copied, 0));
     if (st->dev32)
-        k_full_to_dev32<<<grid_for(N, kBlock), kBlock, 0, s>>>(st->dm, st->phys, st->buf, st->buf.stage);
+        k_full_to_dev32<<<grid_for(N, kBlock), kBlock, 0, s>>>(st->dm, st->phys, st->buf, in);
     else
-        k_scatter_in<<<grid_for(N, kBlock), kBlock, 0, s>>>(st->dm, st->buf.stage, st->buf.psi, 18);
+        k_scatter_in<<<grid_for(N, kBlock), kBlock, 0, s>>>(st->dm, in, st->buf.psi, 18);
     FELBM_CUDA(cudaGetLastError());
+    FELBM_CUDA(cudaEventRecord(st->ev_in_free[k], s));
     // return once the host arrays have been read; the conversion stays queued
     FELBM_CUDA(cudaEventSynchronize(st->ev_copied));
     return FELBM_OK;
@@ -2351,6 +2421,9 @@ void felbm_state_destroy(felbm_state* st) {
     if (st->ev_fork) cudaEventDestroy(st->ev_fork);
     if (st->ev_copied) cudaEventDestroy(st->ev_copied);
     if (st->ev_join) cudaEventDestroy(st->ev_join);
+    if (st->copy_stream) cudaStreamDestroy(st->copy_stream);
+    for (auto& e : st->ev_in_free)
+        if (e) cudaEventDestroy(e);
     for (auto& e : st->ev)
         if (e) cudaEventDestroy(e);
     delete st;

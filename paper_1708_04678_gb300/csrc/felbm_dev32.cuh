@@ -405,19 +405,27 @@ __global__ void k_full_to_dev32(DevMesh m, Phys c, Bufs b, const double* __restr
         C += h[q];
         p += g[q];
     }
-    double rho = c.rho_v + C * (c.rho_l - c.rho_v);
-    double ux = 3.0 * ((g[1] - g[3]) + (g[5] - g[6]) + (g[8] - g[7])) / rho;
-    double uy = 3.0 * ((g[2] - g[4]) + (g[5] + g[6]) - (g[7] + g[8])) / rho;
-    float uxf = (float)ux, uyf = (float)uy, pf = (float)p;
-    // deviations relative to the equilibrium of the stored (rounded) fields
-    double uxs = uxf, uys = uyf, ps = pf;
-    double uu15 = 1.5 * (uxs * uxs + uys * uys);
+    const double jx = (g[1] - g[3]) + (g[5] - g[6]) + (g[8] - g[7]);
+    const double jy = (g[2] - g[4]) + (g[5] + g[6]) - (g[7] + g[8]);
+    const double rho = c.rho_v + C * (c.rho_l - c.rho_v);
+    // the stored fields (FP32 p, u; FP64 C); deviations are taken relative to
+    // the equilibrium of exactly these values
+    const float rhof = (float)rho, Cf = (float)C, pf = (float)p;
+    const float uxf = 3.0f * (float)jx / rhof, uyf = 3.0f * (float)jy / rhof;
+    const double ps = pf;
+    const float uu15 = 1.5f * (uxf * uxf + uyf * uyf);
+    const float r3 = rhof * (1.0f / 3.0f);
+    // g_q - g_q^eq = (g_q - w p) - (rho/3) w T_q and h_q - h_q^eq = (h_q - w C) - w T_q C,
+    // T_q = Gamma_q / w_q - 1 = 3 e.u + 4.5 (e.u)^2 - 1.5 u.u: the large differences in
+    // FP64, the velocity terms (O(|u|) of the state) in FP32
 #pragma unroll
     for (int q = 0; q < 9; ++q) {
-        double eu = ex(q) * uxs + ey(q) * uys;
-        double G = wq(q) * (1.0 + 3.0 * eu + 4.5 * eu * eu - uu15);
-        b.dpsi[q * Np + i] = (float)(g[q] - (wq(q) * ps + rho * (1.0 / 3.0) * (G - wq(q))));
-        b.dpsi[(9 + q) * Np + i] = (float)(h[q] - G * C);
+        const float wf = (float)wq(q);
+        const float eu = (float)ex(q) * uxf + (float)ey(q) * uyf;
+        const float T = 3.0f * eu + 4.5f * eu * eu - uu15;
+        const double dg0 = g[q] - wq(q) * ps, dh0 = h[q] - wq(q) * C;
+        b.dpsi[q * Np + i] = (float)(dg0 - (double)(r3 * (wf * T)));
+        b.dpsi[(9 + q) * Np + i] = (float)(dh0 - (double)((wf * T) * Cf));
     }
     b.C[i] = C;
     b.p32[i] = pf;

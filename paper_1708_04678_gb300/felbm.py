@@ -18,6 +18,7 @@ from . import build as _build
 MAX_WALL_IDS = 256
 LAP_CONSISTENT, LAP_PAPER = 0, 1
 FP64, FP32_DEV = 0, 1
+DIAG_SLOTS = 16          # FELBM_DIAG_SLOTS: raw sums behind one diagnostics record
 SOLVER_MIXED, SOLVER_FP64 = 0, 1
 LAPMU_FACE, LAPMU_NODAL = 0, 1
 
@@ -135,6 +136,8 @@ def _declare(lib):
         "felbm_checkpoint_load": (ctypes.c_int, [_P, _P]),
         "felbm_batch_schedule": (ctypes.c_int, [_P, _I32]),
         "felbm_sweep_parts": (ctypes.c_int, [_P, _I32]),
+        "felbm_diagnostics_enqueue": (ctypes.c_int, [_P, ctypes.POINTER(DiagRequest), _P]),
+        "felbm_diag_finish": (ctypes.c_int, [_P, ctypes.POINTER(DiagRequest), _P, ctypes.POINTER(Diag)]),
         "felbm_autotune": (ctypes.c_int, [_P, _I32, ctypes.POINTER(TuneResult)]),
         "felbm_timing_enable": (ctypes.c_int, [_P, _I32]),
         "felbm_timing_get": (ctypes.c_int, [_P, ctypes.POINTER(StepTiming)]),
@@ -312,6 +315,36 @@ class State:
         req.radius, req.band, req.substrate_wall_id = float(radius), float(band), int(substrate)
         d = Diag()
         code = lib().felbm_diagnostics(self.handle, ctypes.byref(req), ctypes.byref(d))
+        if code not in (0, -5):
+            _check(code)
+        return d.as_dict()
+
+    @staticmethod
+    def _request(centre, radius, band, substrate):
+        req = DiagRequest()
+        if centre is not None:
+            req.centre[0], req.centre[1] = float(centre[0]), float(centre[1])
+        req.radius, req.band, req.substrate_wall_id = float(radius), float(band), int(substrate)
+        return req
+
+    def diagnostics_enqueue(self, slots, centre=None, radius=0.0, band=0.0, substrate=0):
+        """Queue the diagnostics and an asynchronous copy of their raw sums
+        into `slots` (host float64 array or pinned tensor, DIAG_SLOTS values);
+        does not synchronise.  Finish with diag_finish after the stream."""
+        if isinstance(slots, np.ndarray):
+            ok = slots.dtype == np.float64 and slots.flags["C_CONTIGUOUS"] and slots.size >= DIAG_SLOTS
+        else:
+            ok = (not slots.is_cuda and str(slots.dtype) == "torch.float64" and slots.is_contiguous()
+                  and slots.numel() >= DIAG_SLOTS)
+        if not ok:
+            raise ValueError("slots: contiguous host float64 buffer of at least DIAG_SLOTS values")
+        req = self._request(centre, radius, band, substrate)
+        _check(lib().felbm_diagnostics_enqueue(self.handle, ctypes.byref(req), _ptr(slots)))
+
+    def diag_finish(self, slots, centre=None, radius=0.0, band=0.0, substrate=0):
+        req = self._request(centre, radius, band, substrate)
+        d = Diag()
+        code = lib().felbm_diag_finish(self.handle, ctypes.byref(req), _ptr(slots), ctypes.byref(d))
         if code not in (0, -5):
             _check(code)
         return d.as_dict()

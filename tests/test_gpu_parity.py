@@ -203,3 +203,52 @@ def test_bad_workspace_is_rejected():
     small = torch.empty(1024, dtype=torch.uint8, device="cuda")
     with pytest.raises(ValueError):
         F.State(mesh, prm, w["C0"], workspace=small)
+
+
+@pytest.mark.parametrize("precision", [F.FP64, F.FP32_DEV])
+def test_pipelined_inputs_and_async_diagnostics(precision):
+    """Streaming distinct states through one state object: set_state from one
+    pinned host buffer pair that the caller overwrites as soon as the call
+    returns (the copy overlaps the previous step on its own stream, into two
+    input buffers used in turn), a step, and the diagnostics queued with
+    felbm_diagnostics_enqueue and finished after one synchronisation.  Every
+    result equals, bit for bit, the synchronous set_state / step /
+    felbm_diagnostics sequence."""
+    import torch
+    w = WORKLOADS["sessile60"]()
+    src = gpu_state(w, precision=precision)
+    states = []
+    for _ in range(6):
+        src.step(4)
+        states.append(src.get_state())
+    req = dict(centre=w["centre"], radius=w["R"], band=2.0, substrate=0)
+
+    a = gpu_state(w, precision=precision)
+    seq = []
+    for g, h in states:
+        a.set_state(g, h)
+        a.step(3)
+        seq.append(a.diagnostics(**req))
+    ga, ha = a.get_state()
+
+    b = gpu_state(w, precision=precision)
+    gp = torch.empty(states[0][0].shape, dtype=torch.float64).pin_memory()
+    hp = torch.empty(states[0][1].shape, dtype=torch.float64).pin_memory()
+    slots = torch.zeros((len(states), F.DIAG_SLOTS), dtype=torch.float64).pin_memory()
+    for k, (g, h) in enumerate(states):
+        gp.copy_(torch.from_numpy(g))
+        hp.copy_(torch.from_numpy(h))
+        b.set_state(gp, hp)
+        gp.fill_(float("nan"))                    # the host arrays are free once set_state returns
+        hp.fill_(float("nan"))
+        b.step(3)
+        b.diagnostics_enqueue(slots[k], **req)
+    torch.cuda.synchronize()
+    pip = [b.diag_finish(slots[k], **req) for k in range(len(states))]
+    assert pip == seq
+    assert all(d["status"] == 0 for d in pip)
+    gb, hb = b.get_state()
+    np.testing.assert_array_equal(ga, gb)
+    np.testing.assert_array_equal(ha, hb)
+    with pytest.raises(ValueError):
+        b.diagnostics_enqueue(torch.zeros(4, dtype=torch.float64))
