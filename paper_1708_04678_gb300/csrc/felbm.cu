@@ -164,6 +164,7 @@ struct Bufs {
     double* diag_part; // [kDiagBlocks][kDiagSlots]
     double* diag_out;  // [kDiagSlots]
     double* Cdiag;     // [Np]
+    unsigned* diag_done;   // blocks of k_diag_fused32 finished (0 between launches)
 };
 
 constexpr int kBlock = 256;
@@ -710,14 +711,18 @@ template <bool kDev32>
 __device__ __forceinline__ void diag_node(const DevMesh& m, const Phys& c, const Bufs& b, const DiagReq& rq,
                                           int i, double (&s)[10], double (&mx)[1]) {
     const int Np = m.Np;
-    double C = 0, p = 0, ux, uy, rho;
+    double C = 0, p = 0, uu, ruu;
     if (kDev32) {
+        // FP32 fields: |u|^2 and rho |u|^2 in FP32 (FP64 runs at 1/64 rate), summed in FP64
         C = b.C[i];
         p = b.p32[i];
-        ux = b.ux32[i];
-        uy = b.uy32[i];
-        rho = c.rho_v + C * (c.rho_l - c.rho_v);
+        const float uxf = b.ux32[i], uyf = b.uy32[i];
+        const float rhof = c.rho_v_f + (float)C * c.drho_f;
+        const float uuf = uxf * uxf + uyf * uyf;
+        uu = uuf;
+        ruu = rhof * uuf;
         float dsum = 0.0f;
+#pragma unroll
         for (int q = 0; q < 18; ++q) dsum += b.dpsi[q * Np + i];
         if (!isfinite(dsum)) p = dsum;   // non-finite deviations are reported too
     } else {
@@ -730,22 +735,22 @@ __device__ __forceinline__ void diag_node(const DevMesh& m, const Phys& c, const
         }
         double mxm = (g[1] - g[3]) + (g[5] - g[6]) + (g[8] - g[7]);
         double mym = (g[2] - g[4]) + (g[5] + g[6]) - (g[7] + g[8]);
-        rho = c.rho_v + C * (c.rho_l - c.rho_v);
-        ux = 3.0 * mxm / rho;
-        uy = 3.0 * mym / rho;
+        const double rho = c.rho_v + C * (c.rho_l - c.rho_v);
+        const double ux = 3.0 * mxm / rho, uy = 3.0 * mym / rho;
+        uu = ux * ux + uy * uy;
+        ruu = rho * uu;
     }
-    double uu = ux * ux + uy * uy;
     double w = m.lumped[i];
     b.Cdiag[i] = C;
     if (!isfinite(C) || !isfinite(p) || !isfinite(uu)) s[9] += 1.0;
     s[0] += w * C;
-    s[1] += rho * uu;
+    s[1] += ruu;
     if (rq.use_band) {
         double dx = min_image(m.x[i] - rq.cx, rq.period_x), dy = min_image(m.y[i] - rq.cy, rq.period_y);
         double r = sqrt(dx * dx + dy * dy);
         if (fabs(r - rq.R) <= rq.band) {
             s[2] += w;
-            s[3] += w * rho * uu;
+            s[3] += w * ruu;
         }
     }
     if (C >= 0.95) {
@@ -760,9 +765,9 @@ __device__ __forceinline__ void diag_node(const DevMesh& m, const Phys& c, const
 }
 
 // Wetted length of a substrate wall edge (C linear along it).
-__device__ __forceinline__ void diag_wall(const DevMesh& m, const Bufs& b, const DiagReq& rq, int e, double& wet) {
+__device__ __forceinline__ void diag_wall(const DevMesh& m, const double* Cn, const DiagReq& rq, int e, double& wet) {
     if (m.wall_id[e] != rq.substrate) return;
-    double Ca = b.Cdiag[m.wall_a[e]], Cb = b.Cdiag[m.wall_b[e]], L = m.wall_len[e];
+    double Ca = Cn[m.wall_a[e]], Cb = Cn[m.wall_b[e]], L = m.wall_len[e];
     if (Ca >= 0.5 && Cb >= 0.5)
         wet += L;
     else if (Ca >= 0.5 || Cb >= 0.5) {
@@ -772,12 +777,12 @@ __device__ __forceinline__ void diag_wall(const DevMesh& m, const Bufs& b, const
 }
 
 // Highest crossing of the C = 1/2 contour on the edges of a triangle.
-__device__ __forceinline__ void diag_tri(const DevMesh& m, const Bufs& b, const DiagReq& rq, int t, double& ymax) {
+__device__ __forceinline__ void diag_tri(const DevMesh& m, const double* Cn, const DiagReq& rq, int t, double& ymax) {
     const int Tp = m.Tp;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
         int ia = m.tri[((k + 1) % 3) * Tp + t], ic = m.tri[((k + 2) % 3) * Tp + t];
-        double Ca = b.Cdiag[ia], Cc = b.Cdiag[ic];
+        double Ca = Cn[ia], Cc = Cn[ic];
         if ((Ca >= 0.5) != (Cc >= 0.5)) {
             double tt = (0.5 - Ca) / (Cc - Ca);
             double dy = min_image(m.y[ic] - m.y[ia], rq.period_y);
@@ -801,9 +806,9 @@ __global__ void __launch_bounds__(kBlock) k_diag_edges(DevMesh m, Bufs b, DiagRe
     double s[1] = {0.0};
     double mx[1] = {-1e300};
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < m.E; e += gridDim.x * blockDim.x)
-        diag_wall(m, b, rq, e, s[0]);
+        diag_wall(m, b.Cdiag, rq, e, s[0]);
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < m.T; t += gridDim.x * blockDim.x)
-        diag_tri(m, b, rq, t, mx[0]);
+        diag_tri(m, b.Cdiag, rq, t, mx[0]);
     block_reduce_store<1, 1>(s, mx, b.diag_part + (size_t)blockIdx.x * kDiagSlots + 11);
 }
 
@@ -834,8 +839,8 @@ __global__ void __launch_bounds__(kBlock) k_diag_groups(DevMesh m, Phys c, Bufs 
     double we[1] = {0.0};
     double ym[1] = {-1e300};
     for (int k = gt.wall_ptr[g] + threadIdx.x; k < gt.wall_ptr[g + 1]; k += blockDim.x)
-        diag_wall(m, b, rq, gt.wall_edge[k], we[0]);
-    for (int t = gt.tri_begin[g] + threadIdx.x; t < gt.tri_end[g]; t += blockDim.x) diag_tri(m, b, rq, t, ym[0]);
+        diag_wall(m, b.Cdiag, rq, gt.wall_edge[k], we[0]);
+    for (int t = gt.tri_begin[g] + threadIdx.x; t < gt.tri_end[g]; t += blockDim.x) diag_tri(m, b.Cdiag, rq, t, ym[0]);
     block_reduce_store<10, 1>(s, mx, gt.out + (size_t)g * kDiagSlots);
     block_reduce_store<1, 1>(we, ym, gt.out + (size_t)g * kDiagSlots + 11);
 }
@@ -859,6 +864,49 @@ __global__ void k_diag_final(Bufs b) {
     for (int j = 0; j < kPer; ++j) r = is_max ? fmax(r, v[j]) : r + v[j];
     r = is_max ? warp_max(r) : warp_sum(r);
     if (lane == 0) b.diag_out[k] = r;
+}
+
+// FP32-deviation states keep C in FP64, so the edge pass needs no node pass
+// before it: one kernel accumulates every slot, and the last block to finish
+// (a device-scope counter after a fence; no block waits for another) combines
+// the blocks' partials in block order exactly as k_diag_final does.
+__global__ void __launch_bounds__(kBlock) k_diag_fused32(DevMesh m, Phys c, Bufs b, DiagReq rq) {
+    double s[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    double mx[1] = {0.0};
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m.N; i += gridDim.x * blockDim.x)
+        diag_node<true>(m, c, b, rq, i, s, mx);
+    double we[1] = {0.0};
+    double ym[1] = {-1e300};
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < m.E; e += gridDim.x * blockDim.x)
+        diag_wall(m, b.C, rq, e, we[0]);
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < m.T; t += gridDim.x * blockDim.x)
+        diag_tri(m, b.C, rq, t, ym[0]);
+    block_reduce_store<10, 1>(s, mx, b.diag_part + (size_t)blockIdx.x * kDiagSlots);
+    block_reduce_store<1, 1>(we, ym, b.diag_part + (size_t)blockIdx.x * kDiagSlots + 11);
+    __shared__ bool last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(b.diag_done, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    const int lane = threadIdx.x & 31;
+    for (int k = threadIdx.x >> 5; k < kDiagSums; k += kBlock / 32) {
+        const bool is_max = (k == 10 || k == 12);
+        constexpr int kPer = (kDiagBlocks + 31) / 32;
+        double v[kPer];
+#pragma unroll
+        for (int j = 0; j < kPer; ++j) {
+            const int blk = lane + 32 * j;
+            v[j] = blk < kDiagBlocks ? __ldcg(b.diag_part + (size_t)blk * kDiagSlots + k) : (is_max ? -1e300 : 0.0);
+        }
+        double r = is_max ? -1e300 : 0.0;
+#pragma unroll
+        for (int j = 0; j < kPer; ++j) r = is_max ? fmax(r, v[j]) : r + v[j];
+        r = is_max ? warp_max(r) : warp_sum(r);
+        if (lane == 0) b.diag_out[k] = r;
+    }
+    if (threadIdx.x == 0) *b.diag_done = 0u;
 }
 
 // ------------------------------------------- one CTA per batch member ------
@@ -1122,6 +1170,7 @@ static size_t carve(const HostMesh& h, bool dev32, void* base, DevMesh* dm, Bufs
     bb.diag_part = cv.take<double>((size_t)kDiagBlocks * kDiagSlots);
     bb.diag_out = cv.take<double>(kDiagSlots);
     bb.Cdiag = cv.take<double>(Np);
+    bb.diag_done = cv.take<unsigned>(1);
     GroupTables g{};
     const size_t G = std::max<int32_t>(h.G, 1);
     g.node_begin = cv.take<int32_t>(G);
@@ -1587,6 +1636,7 @@ int felbm_init(const felbm_mesh* mesh, const felbm_params* params, const double*
         UP(d.iell_bx32, ibx);
         UP(d.iell_by32, iby);
         if (dev32 && e == cudaSuccess) e = cudaMemsetAsync(st->buf.R32 + (size_t)18 * h.T, 0, 18 * sizeof(float), s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(st->buf.diag_done, 0, sizeof(unsigned), s);
     }
     UP(d.wall_a, h.wall_a);
     UP(d.wall_b, h.wall_b);
@@ -1785,6 +1835,17 @@ static DiagReq make_req(const felbm_state* st, const felbm_diag_request* req) {
 
 // felbm_diag from the reduced slots; the contact angle uses the mean height
 // of the substrate wall nodes among the given wall edges.
+// The diagnostics reductions of the whole mesh into buf.diag_out.
+static void enqueue_diag(felbm_state* st, const DiagReq& rq, cudaStream_t s) {
+    if (st->dev32) {
+        k_diag_fused32<<<kDiagBlocks, kBlock, 0, s>>>(st->dm, st->phys, st->buf, rq);
+        return;
+    }
+    k_diag_nodes<false><<<kDiagBlocks, kBlock, 0, s>>>(st->dm, st->phys, st->buf, rq);
+    k_diag_edges<<<kDiagBlocks, kBlock, 0, s>>>(st->dm, st->buf, rq);
+    k_diag_final<<<1, kDiagSums * 32, 0, s>>>(st->buf);
+}
+
 static felbm_diag fill_diag(const felbm_state* st, const double* v, double mass0, int64_t nodes, int substrate,
                             const int32_t* edges, int32_t n_edges, int64_t step) {
     const HostMesh& h = st->hm;
@@ -1838,12 +1899,7 @@ int felbm_diagnostics(felbm_state* st, const felbm_diag_request* req, felbm_diag
     }
     DiagReq rq = make_req(st, req);
     cudaStream_t s = st->stream;
-    if (st->dev32)
-        k_diag_nodes<true><<<kDiagBlocks, kBlock, 0, s>>>(st->dm, st->phys, st->buf, rq);
-    else
-        k_diag_nodes<false><<<kDiagBlocks, kBlock, 0, s>>>(st->dm, st->phys, st->buf, rq);
-    k_diag_edges<<<kDiagBlocks, kBlock, 0, s>>>(st->dm, st->buf, rq);
-    k_diag_final<<<1, 13 * 32, 0, s>>>(st->buf);
+    enqueue_diag(st, rq, s);
     FELBM_CUDA(cudaGetLastError());
     double v[kDiagSlots];
     FELBM_CUDA(cudaMemcpyAsync(v, st->buf.diag_out, sizeof v, cudaMemcpyDeviceToHost, s));
@@ -1864,12 +1920,7 @@ int felbm_diagnostics_enqueue(felbm_state* st, const felbm_diag_request* req, do
     static_assert(kDiagSlots == FELBM_DIAG_SLOTS, "raw diagnostic sums");
     DiagReq rq = make_req(st, req);
     cudaStream_t s = st->stream;
-    if (st->dev32)
-        k_diag_nodes<true><<<kDiagBlocks, kBlock, 0, s>>>(st->dm, st->phys, st->buf, rq);
-    else
-        k_diag_nodes<false><<<kDiagBlocks, kBlock, 0, s>>>(st->dm, st->phys, st->buf, rq);
-    k_diag_edges<<<kDiagBlocks, kBlock, 0, s>>>(st->dm, st->buf, rq);
-    k_diag_final<<<1, 13 * 32, 0, s>>>(st->buf);
+    enqueue_diag(st, rq, s);
     FELBM_CUDA(cudaGetLastError());
     // the reduced sums arrive asynchronously; the step count is the host's now
     FELBM_CUDA(cudaMemcpyAsync(slots, st->buf.diag_out, sizeof(double) * kDiagSums, cudaMemcpyDeviceToHost, s));

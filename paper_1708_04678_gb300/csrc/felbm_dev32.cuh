@@ -417,15 +417,15 @@ __global__ void k_full_to_dev32(DevMesh m, Phys c, Bufs b, const double* __restr
     const float r3 = rhof * (1.0f / 3.0f);
     // g_q - g_q^eq = (g_q - w p) - (rho/3) w T_q and h_q - h_q^eq = (h_q - w C) - w T_q C,
     // T_q = Gamma_q / w_q - 1 = 3 e.u + 4.5 (e.u)^2 - 1.5 u.u: the large differences in
-    // FP64, the velocity terms (O(|u|) of the state) in FP32
+    // FP64, rounded once to FP32; the velocity terms (O(|u|) of the state) in FP32
 #pragma unroll
     for (int q = 0; q < 9; ++q) {
         const float wf = (float)wq(q);
         const float eu = (float)ex(q) * uxf + (float)ey(q) * uyf;
         const float T = 3.0f * eu + 4.5f * eu * eu - uu15;
-        const double dg0 = g[q] - wq(q) * ps, dh0 = h[q] - wq(q) * C;
-        b.dpsi[q * Np + i] = (float)(dg0 - (double)(r3 * (wf * T)));
-        b.dpsi[(9 + q) * Np + i] = (float)(dh0 - (double)((wf * T) * Cf));
+        const float dg0 = (float)(g[q] - wq(q) * ps), dh0 = (float)(h[q] - wq(q) * C);
+        b.dpsi[q * Np + i] = dg0 - r3 * (wf * T);
+        b.dpsi[(9 + q) * Np + i] = dh0 - (wf * T) * Cf;
     }
     b.C[i] = C;
     b.p32[i] = pf;
