@@ -168,7 +168,7 @@ struct Bufs {
 };
 
 constexpr int kBlock = 256;
-constexpr int kDiagBlocks = 608;   // fixed grid (4 x 152 SMs): the reduction order never changes
+constexpr int kDiagBlocks = 304;   // fixed grid (2 x 152 SMs): the reduction order never changes
 constexpr int kDiagSlots = 16;
 constexpr int kDiagSums = 13;        // slots filled by k_diag_final
 constexpr int kDiagStepSlot = 15;    // felbm_diagnostics_enqueue: the step count
@@ -706,12 +706,24 @@ __device__ void block_reduce_store(double (&s)[NS], double (&mx)[NM], double* ou
     }
 }
 
+// Comparisons of a double with a positive threshold on the bit patterns (the
+// integer pipe; FP64 compares share the 1/64-rate FP64 pipe).  For x >= 0 the
+// patterns order like the values, and every x with the sign bit set is a
+// negative integer, below the pattern of t.  NaNs compare by their pattern;
+// non-finite states are reported through their own slot.
+__device__ __forceinline__ bool ge_pos(double x, double t) { return __double_as_longlong(x) >= __double_as_longlong(t); }
+__device__ __forceinline__ bool le_pos(double x, double t) { return __double_as_longlong(x) <= __double_as_longlong(t); }
+__device__ __forceinline__ bool finite_bits(double x) {
+    return (__double_as_longlong(x) & 0x7ff0000000000000LL) != 0x7ff0000000000000LL;
+}
+
 // Per-node contributions (slots 0..9 sums, one max); writes the node's C.
 template <bool kDev32>
 __device__ __forceinline__ void diag_node(const DevMesh& m, const Phys& c, const Bufs& b, const DiagReq& rq,
                                           int i, double (&s)[10], double (&mx)[1]) {
     const int Np = m.Np;
     double C = 0, p = 0, uu, ruu;
+    bool finite;
     if (kDev32) {
         // FP32 fields: |u|^2 and rho |u|^2 in FP32 (FP64 runs at 1/64 rate), summed in FP64
         C = b.C[i];
@@ -724,7 +736,8 @@ __device__ __forceinline__ void diag_node(const DevMesh& m, const Phys& c, const
         float dsum = 0.0f;
 #pragma unroll
         for (int q = 0; q < 18; ++q) dsum += b.dpsi[q * Np + i];
-        if (!isfinite(dsum)) p = dsum;   // non-finite deviations are reported too
+        // non-finite deviations are reported too
+        finite = finite_bits(C) && isfinite(b.p32[i]) && isfinite(uuf) && isfinite(dsum);
     } else {
         double g[9];
 #pragma unroll
@@ -739,10 +752,11 @@ __device__ __forceinline__ void diag_node(const DevMesh& m, const Phys& c, const
         const double ux = 3.0 * mxm / rho, uy = 3.0 * mym / rho;
         uu = ux * ux + uy * uy;
         ruu = rho * uu;
+        finite = isfinite(C) && isfinite(p) && isfinite(uu);
     }
     double w = m.lumped[i];
     b.Cdiag[i] = C;
-    if (!isfinite(C) || !isfinite(p) || !isfinite(uu)) s[9] += 1.0;
+    if (!finite) s[9] += 1.0;
     s[0] += w * C;
     s[1] += ruu;
     if (rq.use_band) {
@@ -753,11 +767,11 @@ __device__ __forceinline__ void diag_node(const DevMesh& m, const Phys& c, const
             s[3] += w * ruu;
         }
     }
-    if (C >= 0.95) {
+    if (ge_pos(C, 0.95)) {
         s[4] += w;
         s[5] += w * p;
     }
-    if (C <= 0.05) {
+    if (le_pos(C, 0.05)) {
         s[6] += w;
         s[7] += w * p;
     }
@@ -768,9 +782,10 @@ __device__ __forceinline__ void diag_node(const DevMesh& m, const Phys& c, const
 __device__ __forceinline__ void diag_wall(const DevMesh& m, const double* Cn, const DiagReq& rq, int e, double& wet) {
     if (m.wall_id[e] != rq.substrate) return;
     double Ca = Cn[m.wall_a[e]], Cb = Cn[m.wall_b[e]], L = m.wall_len[e];
-    if (Ca >= 0.5 && Cb >= 0.5)
+    const bool a = ge_pos(Ca, 0.5), bb = ge_pos(Cb, 0.5);
+    if (a && bb)
         wet += L;
-    else if (Ca >= 0.5 || Cb >= 0.5) {
+    else if (a || bb) {
         double hi = fmax(Ca, Cb), lo = fmin(Ca, Cb);
         wet += L * (hi - 0.5) / (hi - lo);
     }
@@ -783,7 +798,7 @@ __device__ __forceinline__ void diag_tri(const DevMesh& m, const double* Cn, con
     for (int k = 0; k < 3; ++k) {
         int ia = m.tri[((k + 1) % 3) * Tp + t], ic = m.tri[((k + 2) % 3) * Tp + t];
         double Ca = Cn[ia], Cc = Cn[ic];
-        if ((Ca >= 0.5) != (Cc >= 0.5)) {
+        if (ge_pos(Ca, 0.5) != ge_pos(Cc, 0.5)) {
             double tt = (0.5 - Ca) / (Cc - Ca);
             double dy = min_image(m.y[ic] - m.y[ia], rq.period_y);
             ymax = fmax(ymax, m.y[ia] + tt * dy);
