@@ -506,6 +506,13 @@ def run_gpu(args):
         alg_bytes = N * 4 * 18 * 4 + nnz * (4 + 4) + N * (4 + 4)
         hbm_peak, peak_src = peaks()
         achieved = alg_bytes / (sweep_ms * 1e-3) / 1e9
+        # whole step, with the minimum bytes per node-update of the FP32 form:
+        # distributions read and written (2 x 18 x 4), right-hand side written
+        # and read (2 x 18 x 4), per Chebyshev sweep a gathered iterate, the
+        # residual and the new iterate (3 x 18 x 4), about 200 B of nodal and
+        # element fields
+        k_sweeps = r32["solve_launches"] + 1
+        step_bytes = 2 * 18 * 4 + 2 * 18 * 4 + k_sweeps * 3 * 18 * 4 + 200
 
         def summary(r, dtype):
             return {"value": job_rate(N, K, world, r["total_ms"]), "ms_per_step": r["total_ms"] / K,
@@ -537,6 +544,9 @@ def run_gpu(args):
             "adjoint": radj,
             "large_mesh": rl,
             "tetrahedra_3d": r3,
+            "step_roofline": {"alg_bytes_per_node_update": step_bytes, "sweeps": k_sweeps,
+                              "achieved": s32["value"] * step_bytes / 1e9, "peak": hbm_peak, "unit": "GB/s",
+                              "frac": s32["value"] * step_bytes / 1e9 / hbm_peak},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                          "frac": achieved / hbm_peak, "traffic": recorded_traffic("k_sweep32"),
                          "kernel": "k_sweep32 (one FP32 Chebyshev sweep of the 18-RHS mass solve)",
