@@ -434,6 +434,29 @@ def time_3d(torch, dev, K, flush):
              "phase_ms": {k: round(v, 5) for k, v in ph.items()}, "launches_per_step": st.launches(),
              "after_timed_steps": {k: d[k] for k in ("max_u", "delta_p", "mass_drift_rel", "interface_rho_uu",
                                                      "status")}}
+        # end to end through host buffers, as for the 2D headline: every step
+        # a pinned FP64 state in (overlapping the previous step), one step,
+        # its diagnostics read back asynchronously; all finished in the region
+        g0, h0 = st.get_state()
+        gp = torch.from_numpy(g0).pin_memory()
+        hp = torch.from_numpy(h0).pin_memory()
+        slots = torch.zeros((K, F.DIAG_SLOTS), dtype=torch.float64).pin_memory()
+        st.set_state(gp, hp)
+        st.step(1)
+        st.diagnostics_enqueue(slots[0])
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for k in range(K):
+            st.set_state(gp, hp)
+            st.step(1)
+            st.diagnostics_enqueue(slots[k])
+        stream.synchronize()
+        e2e = [st.diag_finish(slots[k]) for k in range(K)]
+        e2e_s = time.perf_counter() - t0
+        if any(x["status"] != 0 for x in e2e):
+            raise RuntimeError("3D end-to-end steps produced a non-finite state")
+        r["e2e"] = {"value": n * K / e2e_s, "unit": "node-updates/s", "h2d_bytes_per_step": 2 * 19 * n * 8,
+                    "d2h_bytes_per_step": 8 * F.DIAG_SLOTS}
         if prec == F.FP32_DEV:
             sweeps = st.launches() - 4                       # mu, grad mu, element, rhs + the solve
             sweep_ms = ph["solve_ms"] / sweeps

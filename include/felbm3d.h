@@ -100,11 +100,24 @@ int felbm3d_step(felbm3d_state* st, int32_t n_steps);
 /* Global diagnostics of the current state (synchronises the stream). */
 int felbm3d_diagnostics(felbm3d_state* st, const felbm3d_diag_request* req, felbm3d_diag* out);
 
+/* felbm3d_diagnostics in two halves, as felbm_diagnostics_enqueue /
+ * felbm_diag_finish in 2D: the reductions and an asynchronous copy of their
+ * raw sums into `slots` (FELBM_DIAG_SLOTS doubles of caller-owned host
+ * memory, pinned for an asynchronous copy; the last slot receives the step
+ * count) are queued on the state's stream without a synchronisation; once
+ * the stream has passed that point, felbm3d_diag_finish (same req) forms
+ * *out exactly as felbm3d_diagnostics does. */
+int felbm3d_diagnostics_enqueue(felbm3d_state* st, const felbm3d_diag_request* req, double* slots);
+int felbm3d_diag_finish(felbm3d_state* st, const felbm3d_diag_request* req, const double* slots,
+                        felbm3d_diag* out);
+
 /* Copy the distributions to / from host arrays double [19][n_nodes] each
  * (caller order).  FP32_DEV storage converts: get returns psi^eq + dpsi, set
  * recomputes the fields and the FP32 deviations.  get_state synchronises the
- * stream; set_state returns once the host arrays have been read (the
- * conversion stays queued on the stream). */
+ * stream.  set_state copies on a stream of its own into one of two input
+ * buffers used in turn, so the copy overlaps the work already queued on the
+ * state's stream; it returns once the host arrays have been read, and the
+ * conversion stays queued on the state's stream behind that work. */
 int felbm3d_get_state(felbm3d_state* st, double* g, double* h);
 int felbm3d_set_state(felbm3d_state* st, const double* g, const double* h);
 

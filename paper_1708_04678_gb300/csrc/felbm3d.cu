@@ -179,6 +179,8 @@ struct Bufs3 {
     float* lmu32;    // alias of gmu32 (nodal mode)
     float* R32;      // [T][kRow]
     double* stage;   // [38][N] caller-order staging
+    double* in0;     // [38][N] two caller-order input buffers of felbm3d_set_state, used in
+    double* in1;     //         turn so a copy can run while the previous input converts
     double* diag_part; // [kDiagBlocks][kDiagSlots]
     double* diag_out;  // [kDiagSlots]
 };
@@ -915,6 +917,8 @@ static size_t carve3(const HostMesh3D& h, bool dev32, void* base, DevMesh3* dm, 
     b.e0 = cv.take<float>((size_t)kRow * Np);
     b.e1 = cv.take<float>((size_t)kRow * Np);
     b.stage = cv.take<double>(38 * (size_t)h.N);
+    b.in0 = cv.take<double>(38 * (size_t)h.N);
+    b.in1 = cv.take<double>(38 * (size_t)h.N);
     b.diag_part = cv.take<double>(kDiagBlocks * kDiagSlots);
     b.diag_out = cv.take<double>(kDiagSlots);
     if (dm) *dm = d;
@@ -955,6 +959,9 @@ struct felbm3d_state {
     bool use_pdl = true;   // programmatic dependent launch between solve sweeps (FELBM_PDL=0: off)
     cudaEvent_t ev[6] = {};
     cudaEvent_t ev_copied = nullptr;   // set_state: the host arrays have been read
+    cudaStream_t copy_stream = nullptr;     // set_state's host-to-device copies
+    cudaEvent_t ev_in_free[2] = {};         // the conversion that last read buf.in0 / in1 has run
+    int in_next = 0;                        // input buffer of the next set_state
 };
 
 namespace felbm3 {
@@ -1370,14 +1377,22 @@ __global__ void k3_gather_out_f(DevMesh3 m, const float* __restrict__ src, doubl
     if (i < m.N) stage[m.perm[i]] = (double)src[i];
 }
 
-static int diag_run(felbm3d_state* st, const DiagReq3& rq, double* out) {
+// The diagnostics reductions queued on the state's stream, their sums copied
+// to out (host) asynchronously.
+static int diag_enqueue(felbm3d_state* st, const DiagReq3& rq, double* out) {
     cudaStream_t s = st->stream;
     refresh_fields(st);
     k3_diag_partial<<<kDiagBlocks, 256, 0, s>>>(st->dm, st->phys, st->buf, rq);
     k3_diag_final<<<1, 32 * kDiagSlots, 0, s>>>(st->buf);
     FELBM3_CUDA(cudaGetLastError());
     FELBM3_CUDA(cudaMemcpyAsync(out, st->buf.diag_out, sizeof(double) * kDiagSlots, cudaMemcpyDeviceToHost, s));
-    FELBM3_CUDA(cudaStreamSynchronize(s));
+    return FELBM_OK;
+}
+
+static int diag_run(felbm3d_state* st, const DiagReq3& rq, double* out) {
+    int rc = diag_enqueue(st, rq, out);
+    if (rc) return rc;
+    FELBM3_CUDA(cudaStreamSynchronize(st->stream));
     return FELBM_OK;
 }
 
@@ -1404,11 +1419,11 @@ static double substrate_height(const HostMesh3D& h, int id) {
 
 extern "C" {
 
-int felbm3d_diagnostics(felbm3d_state* st, const felbm3d_diag_request* req, felbm3d_diag* out) {
-    if (!st || !out) {
-        set_error("felbm3d_diagnostics: invalid argument");
-        return FELBM_ERR_INVALID_ARG;
-    }
+}  // extern "C"
+
+namespace felbm3 {
+
+static DiagReq3 make_req3(const felbm3d_state* st, const felbm3d_diag_request* req) {
     DiagReq3 rq{};
     rq.substrate = req ? req->substrate_wall_id : -1;
     rq.use_band = req && req->band > 0.0;
@@ -1420,11 +1435,13 @@ int felbm3d_diagnostics(felbm3d_state* st, const felbm3d_diag_request* req, felb
         rq.radius = req->radius;
         rq.band = req->band;
     }
-    double v[kDiagSlots];
-    int rc = diag_run(st, rq, v);
-    if (rc) return rc;
+    return rq;
+}
+
+// felbm3d_diag from the reduced sums v of the step `step`.
+static felbm3d_diag fill_diag3(const felbm3d_state* st, const DiagReq3& rq, const double* v, int64_t step) {
     felbm3d_diag d{};
-    d.step = st->step;
+    d.step = step;
     d.mass = v[0];
     d.mass0 = st->mass0;
     d.mass_drift_rel = (v[0] - st->mass0) / st->mass0;
@@ -1450,7 +1467,45 @@ int felbm3d_diagnostics(felbm3d_state* st, const felbm3d_diag_request* req, felb
         }
     }
     d.status = v[11] > 0.0 ? FELBM_ERR_NONFINITE : FELBM_OK;
-    *out = d;
+    return d;
+}
+
+}  // namespace felbm3
+
+extern "C" {
+
+int felbm3d_diagnostics(felbm3d_state* st, const felbm3d_diag_request* req, felbm3d_diag* out) {
+    if (!st || !out) {
+        set_error("felbm3d_diagnostics: invalid argument");
+        return FELBM_ERR_INVALID_ARG;
+    }
+    const DiagReq3 rq = make_req3(st, req);
+    double v[kDiagSlots];
+    int rc = diag_run(st, rq, v);
+    if (rc) return rc;
+    *out = fill_diag3(st, rq, v, st->step);
+    return FELBM_OK;
+}
+
+int felbm3d_diagnostics_enqueue(felbm3d_state* st, const felbm3d_diag_request* req, double* slots) {
+    if (!st || !slots) {
+        set_error("felbm3d_diagnostics_enqueue: invalid argument");
+        return FELBM_ERR_INVALID_ARG;
+    }
+    static_assert(kDiagSlots < FELBM_DIAG_SLOTS, "raw diagnostic sums and the step");
+    int rc = diag_enqueue(st, make_req3(st, req), slots);
+    if (rc) return rc;
+    slots[FELBM_DIAG_SLOTS - 1] = (double)st->step;
+    return FELBM_OK;
+}
+
+int felbm3d_diag_finish(felbm3d_state* st, const felbm3d_diag_request* req, const double* slots,
+                        felbm3d_diag* out) {
+    if (!st || !slots || !out) {
+        set_error("felbm3d_diag_finish: invalid argument");
+        return FELBM_ERR_INVALID_ARG;
+    }
+    *out = fill_diag3(st, make_req3(st, req), slots, (int64_t)slots[FELBM_DIAG_SLOTS - 1]);
     return FELBM_OK;
 }
 
@@ -1479,15 +1534,27 @@ int felbm3d_set_state(felbm3d_state* st, const double* g, const double* h) {
     }
     cudaStream_t s = st->stream;
     const size_t N = st->hm.N;
-    FELBM3_CUDA(cudaMemcpyAsync(st->buf.stage, g, sizeof(double) * 19 * N, cudaMemcpyDefault, s));
-    FELBM3_CUDA(cudaMemcpyAsync(st->buf.stage + 19 * N, h, sizeof(double) * 19 * N, cudaMemcpyDefault, s));
+    if (!st->copy_stream) FELBM3_CUDA(cudaStreamCreateWithFlags(&st->copy_stream, cudaStreamNonBlocking));
     if (!st->ev_copied) FELBM3_CUDA(cudaEventCreateWithFlags(&st->ev_copied, cudaEventDisableTiming));
-    FELBM3_CUDA(cudaEventRecord(st->ev_copied, s));
+    for (auto& ev : st->ev_in_free)
+        if (!ev) FELBM3_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    // the copy runs on its own stream into the input buffer the previous call
+    // did not use, overlapping the work queued on the state's stream; it waits
+    // only for the conversion that last read this buffer
+    const int k = st->in_next;
+    st->in_next ^= 1;
+    double* in = k ? st->buf.in1 : st->buf.in0;
+    FELBM3_CUDA(cudaStreamWaitEvent(st->copy_stream, st->ev_in_free[k], 0));
+    FELBM3_CUDA(cudaMemcpyAsync(in, g, sizeof(double) * 19 * N, cudaMemcpyDefault, st->copy_stream));
+    FELBM3_CUDA(cudaMemcpyAsync(in + 19 * N, h, sizeof(double) * 19 * N, cudaMemcpyDefault, st->copy_stream));
+    FELBM3_CUDA(cudaEventRecord(st->ev_copied, st->copy_stream));
+    FELBM3_CUDA(cudaStreamWaitEvent(s, st->ev_copied, 0));
     if (st->dev32)
-        k3_stage_to_dev32<<<grid_for(st->dm.N, kNodeBlock), kNodeBlock, 0, s>>>(st->dm, st->phys, st->buf);
+        k3_stage_to_dev32<<<grid_for(st->dm.N, kNodeBlock), kNodeBlock, 0, s>>>(st->dm, st->phys, st->buf, in);
     else
-        k3_scatter_in<<<grid_for(st->dm.N, kBlock), kBlock, 0, s>>>(st->dm, st->buf.stage, st->buf.psi, 38);
+        k3_scatter_in<<<grid_for(st->dm.N, kBlock), kBlock, 0, s>>>(st->dm, in, st->buf.psi, 38);
     FELBM3_CUDA(cudaGetLastError());
+    FELBM3_CUDA(cudaEventRecord(st->ev_in_free[k], s));
     refresh_fields(st);
     // return once the host arrays have been read; the conversion stays queued
     FELBM3_CUDA(cudaEventSynchronize(st->ev_copied));
@@ -1530,6 +1597,9 @@ void felbm3d_state_destroy(felbm3d_state* st) {
     for (auto& ev : st->ev)
         if (ev) cudaEventDestroy(ev);
     if (st->ev_copied) cudaEventDestroy(st->ev_copied);
+    if (st->copy_stream) cudaStreamDestroy(st->copy_stream);
+    for (auto& e : st->ev_in_free)
+        if (e) cudaEventDestroy(e);
     delete st;
 }
 

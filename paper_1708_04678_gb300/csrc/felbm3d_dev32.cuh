@@ -439,15 +439,15 @@ __global__ void k3_dev32_to_stage(DevMesh3 m, Phys3 c, Bufs3 b) {
     }
 }
 
-// fields and deviations from full FP64 distributions staged in caller order
-__global__ void k3_stage_to_dev32(DevMesh3 m, Phys3 c, Bufs3 b) {
+// fields and deviations from full FP64 distributions (src [38][N], caller order)
+__global__ void k3_stage_to_dev32(DevMesh3 m, Phys3 c, Bufs3 b, const double* __restrict__ src) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= m.N) return;
     const size_t N = m.N, o = m.perm[i];
     double C = 0.0, p = 0.0, mx = 0.0, my = 0.0, mz = 0.0;
     for (int q = 0; q < 19; ++q) {
-        double g = b.stage[(size_t)q * N + o];
-        C += b.stage[(size_t)(19 + q) * N + o];
+        double g = src[(size_t)q * N + o];
+        C += src[(size_t)(19 + q) * N + o];
         p += g;
         mx += edot3(q, g, 0.0, 0.0);
         my += edot3(q, 0.0, g, 0.0);
@@ -460,8 +460,8 @@ __global__ void k3_stage_to_dev32(DevMesh3 m, Phys3 c, Bufs3 b) {
     for (int q = 0; q < 19; ++q) {
         double eu = edot3(q, ux, uy, uz);
         double G = wq3(q) * (1.0 + 3.0 * eu + 4.5 * eu * eu - uu15);
-        d[slot(0, q)] = (float)(b.stage[(size_t)q * N + o] - (wq3(q) * p + rho * (1.0 / 3.0) * (G - wq3(q))));
-        d[slot(1, q)] = (float)(b.stage[(size_t)(19 + q) * N + o] - G * C);
+        d[slot(0, q)] = (float)(src[(size_t)q * N + o] - (wq3(q) * p + rho * (1.0 / 3.0) * (G - wq3(q))));
+        d[slot(1, q)] = (float)(src[(size_t)(19 + q) * N + o] - G * C);
     }
     d[slot(0, 19)] = 0.0f;
     d[slot(1, 19)] = 0.0f;

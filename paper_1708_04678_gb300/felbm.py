@@ -167,6 +167,17 @@ def _check(code):
         raise FelbmError(code, lib().felbm_last_error().decode())
 
 
+def check_slots(slots):
+    """A diagnostics slot buffer: contiguous host float64, at least DIAG_SLOTS values."""
+    if isinstance(slots, np.ndarray):
+        ok = slots.dtype == np.float64 and slots.flags["C_CONTIGUOUS"] and slots.size >= DIAG_SLOTS
+    else:
+        ok = (not slots.is_cuda and str(slots.dtype) == "torch.float64" and slots.is_contiguous()
+              and slots.numel() >= DIAG_SLOTS)
+    if not ok:
+        raise ValueError("slots: contiguous host float64 buffer of at least DIAG_SLOTS values")
+
+
 def _ptr(a):
     """Host or device address of a numpy array or torch tensor."""
     if a is None:
@@ -331,13 +342,7 @@ class State:
         """Queue the diagnostics and an asynchronous copy of their raw sums
         into `slots` (host float64 array or pinned tensor, DIAG_SLOTS values);
         does not synchronise.  Finish with diag_finish after the stream."""
-        if isinstance(slots, np.ndarray):
-            ok = slots.dtype == np.float64 and slots.flags["C_CONTIGUOUS"] and slots.size >= DIAG_SLOTS
-        else:
-            ok = (not slots.is_cuda and str(slots.dtype) == "torch.float64" and slots.is_contiguous()
-                  and slots.numel() >= DIAG_SLOTS)
-        if not ok:
-            raise ValueError("slots: contiguous host float64 buffer of at least DIAG_SLOTS values")
+        check_slots(slots)
         req = self._request(centre, radius, band, substrate)
         _check(lib().felbm_diagnostics_enqueue(self.handle, ctypes.byref(req), _ptr(slots)))
 

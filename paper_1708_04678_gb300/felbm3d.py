@@ -58,6 +58,9 @@ def lib():
                                             ctypes.POINTER(_P)]),
             "felbm3d_step": (ctypes.c_int, [_P, _I32]),
             "felbm3d_diagnostics": (ctypes.c_int, [_P, ctypes.POINTER(DiagRequest3D), ctypes.POINTER(Diag3D)]),
+            "felbm3d_diagnostics_enqueue": (ctypes.c_int, [_P, ctypes.POINTER(DiagRequest3D), _P]),
+            "felbm3d_diag_finish": (ctypes.c_int, [_P, ctypes.POINTER(DiagRequest3D), _P,
+                                                   ctypes.POINTER(Diag3D)]),
             "felbm3d_get_state": (ctypes.c_int, [_P, _P, _P]),
             "felbm3d_set_state": (ctypes.c_int, [_P, _P, _P]),
             "felbm3d_get_fields": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P]),
@@ -149,16 +152,34 @@ class State3D:
     def step(self, n=1):
         _check(lib().felbm3d_step(self.handle, int(n)))
 
-    def diagnostics(self, centre=None, radius=0.0, band=0.0, substrate=0):
+    @staticmethod
+    def _request(centre, radius, band, substrate):
         req = DiagRequest3D()
         if centre is not None:
             for k in range(3):
                 req.centre[k] = float(centre[k])
         req.radius, req.band, req.substrate_wall_id = float(radius), float(band), int(substrate)
+        return req
+
+    def diagnostics(self, centre=None, radius=0.0, band=0.0, substrate=0):
+        req = self._request(centre, radius, band, substrate)
         d = Diag3D()
         code = lib().felbm3d_diagnostics(self.handle, ctypes.byref(req), ctypes.byref(d))
         if code != 0:
             _check(code)
+        return d.as_dict()
+
+    def diagnostics_enqueue(self, slots, centre=None, radius=0.0, band=0.0, substrate=0):
+        """Queue the diagnostics and an asynchronous copy of their raw sums into
+        `slots` (host float64, F.DIAG_SLOTS values); finish with diag_finish."""
+        F.check_slots(slots)
+        req = self._request(centre, radius, band, substrate)
+        _check(lib().felbm3d_diagnostics_enqueue(self.handle, ctypes.byref(req), _ptr(slots)))
+
+    def diag_finish(self, slots, centre=None, radius=0.0, band=0.0, substrate=0):
+        req = self._request(centre, radius, band, substrate)
+        d = Diag3D()
+        _check(lib().felbm3d_diag_finish(self.handle, ctypes.byref(req), _ptr(slots), ctypes.byref(d)))
         return d.as_dict()
 
     def get_state(self, g=None, h=None):
