@@ -694,6 +694,14 @@ __device__ __forceinline__ double wet_fraction_area(double A, double c0, double 
 
 __device__ __forceinline__ double min_image_d(double d, double L) { return L > 0.0 ? d - L * rint(d / L) : d; }
 
+// x >= t and x <= t for a positive threshold t, on the bit patterns (integer
+// pipe; FP64 compares share the 1/64-rate FP64 pipe): for x >= 0 the patterns
+// order like the values, and any x with the sign bit set is a negative
+// integer, below the pattern of t.  NaNs compare by their pattern; non-finite
+// states are counted in their own slot.
+__device__ __forceinline__ bool ge_pos3(double x, double t) { return __double_as_longlong(x) >= __double_as_longlong(t); }
+__device__ __forceinline__ bool le_pos3(double x, double t) { return __double_as_longlong(x) <= __double_as_longlong(t); }
+
 // slots: 0 sum m C, 1 sum rho |u|^2, 2 max |u|^2, 3-4 sum m p / sum m over
 // C >= 0.95, 5-6 the same over C <= 0.05, 7-8 sum m rho|u|^2 / sum m over the
 // band, 9 wetted area, 10 max height of a C = 1/2 crossing, 11 non-finite count
@@ -724,10 +732,10 @@ __global__ void __launch_bounds__(256) k3_diag_partial(DevMesh3 m, Phys3 c, Bufs
         s[0] += lw * C;
         s[1] += rho * uu;
         s[2] = fmax(s[2], uu);
-        if (C >= 0.95) {
+        if (ge_pos3(C, 0.95)) {
             s[3] += lw * p;
             s[4] += lw;
-        } else if (C <= 0.05) {
+        } else if (le_pos3(C, 0.05)) {
             s[5] += lw * p;
             s[6] += lw;
         }
@@ -756,7 +764,7 @@ __global__ void __launch_bounds__(256) k3_diag_partial(DevMesh3 m, Phys3 c, Bufs
 #pragma unroll
                 for (int e = a + 1; e < 4; ++e) {
                     double Ca = b.C[v[a]], Cb = b.C[v[e]];
-                    if ((Ca >= 0.5) != (Cb >= 0.5)) {
+                    if (ge_pos3(Ca, 0.5) != ge_pos3(Cb, 0.5)) {
                         double w = (0.5 - Ca) / (Cb - Ca);
                         double dz = min_image_d(m.z[v[e]] - m.z[v[a]], m.period[2]);
                         s[10] = fmax(s[10], m.z[v[a]] + w * dz);
@@ -764,23 +772,28 @@ __global__ void __launch_bounds__(256) k3_diag_partial(DevMesh3 m, Phys3 c, Bufs
                 }
         }
     }
-    // block reduction: warp shuffles, then the 8 warps in a fixed order
-    __shared__ double red[8][kDiagSlots];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // block reduction in a fixed order, every partial added once (FP64 adds
+    // run at 1/64 rate): the threads' partials through shared memory, 8
+    // threads per slot over interleaved segments of 32, then one per slot
+    constexpr int kSeg = 8, kL = 256 + 2;
+    __shared__ double sh[kDiagSlots][kL];
+    __shared__ double part[kDiagSlots][kSeg];
 #pragma unroll
-    for (int k = 0; k < kDiagSlots; ++k) {
-        double v = s[k];
-        for (int o = 16; o > 0; o >>= 1) {
-            double w = __shfl_down_sync(0xffffffffu, v, o);
-            v = (k == 2 || k == 10) ? fmax(v, w) : v + w;
-        }
-        if (lane == 0) red[warp][k] = v;
+    for (int k = 0; k < kDiagSlots; ++k) sh[k][threadIdx.x] = s[k];
+    __syncthreads();
+    if (threadIdx.x < kDiagSlots * kSeg) {
+        const int k = threadIdx.x / kSeg, seg = threadIdx.x - k * kSeg;
+        const bool is_max = k == 2 || k == 10;
+        double v = sh[k][seg];
+        for (int j = 1; j < 32; ++j) v = is_max ? fmax(v, sh[k][seg + kSeg * j]) : v + sh[k][seg + kSeg * j];
+        part[k][seg] = v;
     }
     __syncthreads();
     if (threadIdx.x < kDiagSlots) {
         const int k = threadIdx.x;
-        double v = red[0][k];
-        for (int w = 1; w < 8; ++w) v = (k == 2 || k == 10) ? fmax(v, red[w][k]) : v + red[w][k];
+        const bool is_max = k == 2 || k == 10;
+        double v = part[k][0];
+        for (int w = 1; w < kSeg; ++w) v = is_max ? fmax(v, part[k][w]) : v + part[k][w];
         b.diag_part[blockIdx.x * kDiagSlots + k] = v;
     }
 }

@@ -439,37 +439,58 @@ __global__ void k3_dev32_to_stage(DevMesh3 m, Phys3 c, Bufs3 b) {
     }
 }
 
-// fields and deviations from full FP64 distributions (src [38][N], caller order)
+// fields and deviations from full FP64 distributions (src [38][N], caller
+// order).  C, p and the momentum are summed in FP64; the stored fields are
+// FP32 p, u and FP64 C, and the deviations are taken relative to the
+// equilibrium of exactly these values:
+//   g_q - g_q^eq = (g_q - w p) - (rho/3) w T_q,  h_q - h_q^eq = (h_q - w C) - w T_q C,
+// T_q = Gamma_q / w_q - 1 = 3 e.u + 4.5 (e.u)^2 - 1.5 u.u.  The large
+// differences are taken in FP64 and rounded once; the velocity terms, O(|u|)
+// of the state, in FP32 (FP64 runs at 1/64 of the FP32 rate).
 __global__ void k3_stage_to_dev32(DevMesh3 m, Phys3 c, Bufs3 b, const double* __restrict__ src) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= m.N) return;
     const size_t N = m.N, o = m.perm[i];
-    double C = 0.0, p = 0.0, mx = 0.0, my = 0.0, mz = 0.0;
+    double g[19], h[19], C = 0.0, p = 0.0, jx = 0.0, jy = 0.0, jz = 0.0;
+#pragma unroll
     for (int q = 0; q < 19; ++q) {
-        double g = src[(size_t)q * N + o];
-        C += src[(size_t)(19 + q) * N + o];
-        p += g;
-        mx += edot3(q, g, 0.0, 0.0);
-        my += edot3(q, 0.0, g, 0.0);
-        mz += edot3(q, 0.0, 0.0, g);
+        g[q] = src[(size_t)q * N + o];
+        h[q] = src[(size_t)(19 + q) * N + o];
+        C += h[q];
+        p += g[q];
+    }
+#pragma unroll
+    for (int q = 1; q < 19; ++q) {   // e_q components are 0 or +-1
+        if (ex3(q) == 1) jx += g[q];
+        if (ex3(q) == -1) jx -= g[q];
+        if (ey3(q) == 1) jy += g[q];
+        if (ey3(q) == -1) jy -= g[q];
+        if (ez3(q) == 1) jz += g[q];
+        if (ez3(q) == -1) jz -= g[q];
     }
     const double rho = c.rho_v + C * (c.rho_l - c.rho_v);
-    const double ux = 3.0 * mx / rho, uy = 3.0 * my / rho, uz = 3.0 * mz / rho;
-    const double uu15 = 1.5 * (ux * ux + uy * uy + uz * uz);
+    const float rhof = (float)rho, Cf = (float)C, pf = (float)p;
+    const float uxf = 3.0f * (float)jx / rhof, uyf = 3.0f * (float)jy / rhof, uzf = 3.0f * (float)jz / rhof;
+    const double ps = pf;
+    const float uu15 = 1.5f * (uxf * uxf + uyf * uyf + uzf * uzf);
+    const float r3 = rhof * (1.0f / 3.0f);
     float* d = b.dpsi + (size_t)i * kRow;
+#pragma unroll
     for (int q = 0; q < 19; ++q) {
-        double eu = edot3(q, ux, uy, uz);
-        double G = wq3(q) * (1.0 + 3.0 * eu + 4.5 * eu * eu - uu15);
-        d[slot(0, q)] = (float)(src[(size_t)q * N + o] - (wq3(q) * p + rho * (1.0 / 3.0) * (G - wq3(q))));
-        d[slot(1, q)] = (float)(src[(size_t)(19 + q) * N + o] - G * C);
+        const float wf = (float)wq3(q);
+        const float eu = (float)ex3(q) * uxf + (float)ey3(q) * uyf + (float)ez3(q) * uzf;
+        const float T = 3.0f * eu + 4.5f * eu * eu - uu15;
+        const float dg0 = (float)(g[q] - wq3(q) * ps), dh0 = (float)(h[q] - wq3(q) * C);
+        d[slot(0, q)] = dg0 - r3 * (wf * T);
+        d[slot(1, q)] = dh0 - (wf * T) * Cf;
     }
     d[slot(0, 19)] = 0.0f;
     d[slot(1, 19)] = 0.0f;
     b.C[i] = C;
-    b.p32[i] = (float)p;
-    b.ux32[i] = (float)ux;
-    b.uy32[i] = (float)uy;
-    b.uz32[i] = (float)uz;
+    b.p32[i] = pf;
+    b.ux32[i] = uxf;
+    b.uy32[i] = uyf;
+    b.uz32[i] = uzf;
 }
 
 // rest state from C0 staged in caller order: C = C0, p = u = 0, dpsi = 0
