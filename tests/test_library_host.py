@@ -143,3 +143,19 @@ def test_mesh3d_validation(lib):
     with pytest.raises(F.FelbmError) as e:                                 # wall id beyond the table
         F3.Mesh3D(xyz, [[0, 1, 2, 3]], faces, [0, 0, 0, F.MAX_WALL_IDS])
     assert e.value.code == -1
+
+
+def test_diag_slot_buffers_are_validated(lib):
+    """The queued-diagnostics binding takes only contiguous host float64
+    buffers of at least FELBM_DIAG_SLOTS values (the library copies that many
+    sums into them asynchronously)."""
+    torch = pytest.importorskip("torch")
+    hdr = open(os.path.join(B.INCLUDE, "felbm.h")).read()
+    assert int(re.search(r"#define FELBM_DIAG_SLOTS (\d+)", hdr).group(1)) == F.DIAG_SLOTS
+    F.check_slots(np.zeros(F.DIAG_SLOTS))
+    F.check_slots(torch.zeros((3, F.DIAG_SLOTS), dtype=torch.float64)[1])
+    for bad in (np.zeros(F.DIAG_SLOTS - 1), np.zeros(F.DIAG_SLOTS, dtype=np.float32),
+                np.zeros((F.DIAG_SLOTS, 2))[:, 0], torch.zeros(F.DIAG_SLOTS, dtype=torch.float32),
+                torch.zeros((F.DIAG_SLOTS, 2), dtype=torch.float64)[:, 0]):
+        with pytest.raises(ValueError):
+            F.check_slots(bad)
