@@ -319,3 +319,79 @@ def rough_wall_droplet(seed=4, width=2048, height=1024, rows=1017, R=300.0,
     C0 = droplet_C0(mesh["xy"], centre, R, phys["xi"], mesh["period"])
     return {"name": f"rough-wall droplet {width}x{height}", "mesh": mesh, "C0": C0,
             "phys": phys, "steps": steps, "centre": centre, "R": float(R)}
+
+
+def capillary_channel(H=16, length_factor=20, reservoir=4, theta=56.0, l0_factor=2.0, liquid_factor=4.0,
+                      ratio=10.0, dt=0.1, sigma=0.01, xi=2.0, mobility=0.02, jitter=0.0, seed=6):
+    """Capillary intrusion, the 2D analogue of Sec. III.C: a box periodic in x
+    and y holding one solid block with a straight channel of width H and
+    length length_factor*H through it (wall id 0 on every face of the block,
+    wetting angle theta); outside the channel's x-range the fluid is open and
+    periodic.  Liquid fills a slab of liquid_factor*H to the left of the
+    entrance and the first l0_factor*H of the channel (flat meniscus); vapour
+    fills the rest.  Grid points (i, j) with h = 1, two triangles per cell;
+    cells inside the block are left out.  Returns the workload dict and the
+    channel geometry (x of the entrance ``x_in``, centre line ``y_c``, H)."""
+    Lc = int(length_factor * H)
+    res = int(reservoir * H)
+    nx = Lc + 2 * res
+    ny = 3 * H
+    i0, i1 = res, res + Lc                 # channel x-range (cells)
+    j0, j1 = H, 2 * H                      # channel y-range (cells)
+
+    ci, cj = np.meshgrid(np.arange(nx), np.arange(ny), indexing="xy")
+    solid = (ci >= i0) & (ci < i1) & ((cj < j0) | (cj >= j1))
+    keep = ~solid
+    # nodes used by a kept cell (periodic in both directions)
+    used = np.zeros((ny, nx), dtype=bool)
+    for di in (0, 1):
+        for dj in (0, 1):
+            used[(cj + dj) % ny, (ci + di) % nx] |= keep
+    node_id = -np.ones((ny, nx), dtype=np.int64)
+    node_id[used] = np.arange(int(used.sum()))
+    jj, ii = np.nonzero(used)
+    xy = np.stack([ii.astype(np.float64), jj.astype(np.float64)], axis=1)
+
+    def nid(a, b):
+        return node_id[b % ny, a % nx]
+
+    kc_j, kc_i = np.nonzero(keep)
+    n00, n10 = nid(kc_i, kc_j), nid(kc_i + 1, kc_j)
+    n11, n01 = nid(kc_i + 1, kc_j + 1), nid(kc_i, kc_j + 1)
+    tri = np.empty((2 * len(kc_i), 3), dtype=np.int32)
+    tri[0::2] = np.stack([n00, n10, n11], axis=1)
+    tri[1::2] = np.stack([n00, n11, n01], axis=1)
+
+    # wall edges: cell sides between a kept cell and a solid one
+    walls = []
+    for a, b in zip(kc_i, kc_j):
+        if solid[(b - 1) % ny, a]:
+            walls.append((nid(a, b), nid(a + 1, b)))
+        if solid[(b + 1) % ny, a]:
+            walls.append((nid(a, b + 1), nid(a + 1, b + 1)))
+        if solid[b, (a - 1) % nx]:
+            walls.append((nid(a, b), nid(a, b + 1)))
+        if solid[b, (a + 1) % nx]:
+            walls.append((nid(a + 1, b), nid(a + 1, b + 1)))
+    wall_edges = np.asarray(walls, dtype=np.int32)
+    wall_id = np.zeros(len(walls), dtype=np.int32)
+
+    if jitter > 0.0:
+        rng = np.random.default_rng(seed)
+        on_wall = np.zeros(len(xy), dtype=bool)
+        on_wall[wall_edges.ravel()] = True
+        jit = rng.uniform(-jitter, jitter, size=xy.shape)
+        jit[on_wall] = 0.0
+        xy = xy + jit
+
+    period = (float(nx), float(ny))
+    phys = _phys(dt=dt, rho_v=1.0 / ratio, sigma=sigma, xi=xi, mobility=mobility, theta_deg=(theta,))
+    x_in = float(i0)
+    xa = x_in - liquid_factor * H
+    xm = x_in + l0_factor * H
+    d = np.minimum(xy[:, 0] - xa, xm - xy[:, 0])
+    C0 = 0.5 + 0.5 * np.tanh(2.0 * d / xi)
+    mesh = {"xy": xy, "tri": tri, "wall_edges": wall_edges, "wall_id": wall_id, "period": period,
+            "n_grid_points": int(used.sum()), "min_area": float(_triangle_areas(xy, tri, period).min())}
+    return {"name": f"capillary channel H={H}, theta={theta}", "mesh": mesh, "C0": C0, "phys": phys,
+            "x_in": x_in, "y_c": 1.5 * H, "H": float(H), "length": float(Lc), "l0": l0_factor * H}

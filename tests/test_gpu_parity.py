@@ -66,6 +66,9 @@ WORKLOADS = {
     "sessile120_paper": lambda: I.small_sessile(nx=36, ny=18, R=8.0, theta=120.0),
     "free_droplet": lambda: I.small_free_droplet(n=24, R=6.0),
     "rough_wall": _rough_small,
+    # internal walls with re-entrant corners (a block with a channel through it)
+    "channel": lambda: I.capillary_channel(H=6, length_factor=6, reservoir=2, theta=56.0, l0_factor=1.0,
+                                           liquid_factor=1.5, dt=0.1, xi=2.0),
 }
 
 
@@ -82,7 +85,7 @@ def test_single_step(name):
 
 
 @pytest.mark.parametrize("name,steps", [("sessile60", 300), ("free_droplet", 300),
-                                        ("rough_wall", 150), ("sessile120_paper", 200)])
+                                        ("rough_wall", 150), ("sessile120_paper", 200), ("channel", 150)])
 def test_multi_step(name, steps):
     w = WORKLOADS[name]()
     lap = "paper" if name.endswith("paper") else "consistent"
