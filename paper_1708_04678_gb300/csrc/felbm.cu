@@ -26,7 +26,9 @@
 //               weak bounce-back on walls; first Chebyshev iterate
 //   k_cheb      Chebyshev sweeps of the consistent-mass solve with the
 //               lumped-mass preconditioner; the last adds the increment
-// No atomics anywhere: every sum is a fixed-order loop or tree.
+// No floating-point atomics: every sum is a fixed-order loop or tree.  The one
+// atomic is an integer counter that picks the block of k_diag_fused32 that
+// combines the blocks' partials (in block order, whichever block it is).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -170,7 +172,7 @@ struct Bufs {
 constexpr int kBlock = 256;
 constexpr int kDiagBlocks = 304;   // fixed grid (2 x 152 SMs): the reduction order never changes
 constexpr int kDiagSlots = 16;
-constexpr int kDiagSums = 13;        // slots filled by k_diag_final
+constexpr int kDiagSums = 13;        // slots of the final reduction (k_diag_final, or k_diag_fused32's last block)
 constexpr int kDiagStepSlot = 15;    // felbm_diagnostics_enqueue: the step count
 
 // ------------------------------------------------------ K1: collision -----
