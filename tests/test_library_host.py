@@ -159,3 +159,19 @@ def test_diag_slot_buffers_are_validated(lib):
                 torch.zeros((F.DIAG_SLOTS, 2), dtype=torch.float64)[:, 0]):
         with pytest.raises(ValueError):
             F.check_slots(bad)
+
+
+def test_channel_mesh_with_a_hole(lib):
+    """The capillary-channel geometry: a periodic box with a solid block and a
+    channel through it.  Every boundary edge is a declared wall (the library
+    accepts the mesh), the wall count is the block's perimeter in cells (two
+    channel walls of length L, two end faces of height 2H) and the fluid area
+    is the box minus the block."""
+    H, lf, res = 4, 4, 2
+    w = I.capillary_channel(H=H, length_factor=lf, reservoir=res, xi=2.0)
+    info = F.Mesh.from_dict(w["mesh"]).info()
+    L = lf * H
+    nx, ny = L + 2 * res * H, 3 * H
+    assert info["n_wall_edges"] == 2 * L + 2 * (2 * H)
+    assert abs(info["total_area"] - (nx * ny - L * 2 * H)) < 1e-9
+    assert info["n_groups"] == 1
