@@ -29,7 +29,9 @@ its reason in the design notes of the repository):
 Parity status: every function here is pinned by ``tests/test_oracle_*.py``
 against closed forms, brute-force quadrature, invariants or physical laws
 (static-interface balance, exact mass conservation, Laplace, Young); the
-trajectory after many steps has no independent pin beyond those.
+element Laplacian of mu of Sec. II.D against hand-derived stencils on the
+unjittered grids, the forces against their zeroth and first lattice moments;
+the trajectory after many steps has no independent pin beyond those.
 """
 from __future__ import annotations
 
