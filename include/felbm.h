@@ -318,9 +318,11 @@ int felbm_mass_solve(felbm_state* state, const double* B, double* X, int32_t k);
 
 /* felbm_mass_solve without any device allocation, for callers that cannot
  * allocate: code running where cudaMalloc is not allowed or not wanted (a
- * host callback, a stream-ordered section that must not synchronise, a
- * plugin whose host application owns all device memory) and that cannot
- * lend the state's workspace either, because felbm_step may be using it.
+ * stream-ordered section that must not synchronise, a plugin whose host
+ * application owns all device memory) and that cannot lend the state's
+ * workspace either, because felbm_step may be using it.  It enqueues CUDA
+ * work, so it must not be called from inside a stream callback
+ * (cudaLaunchHostFunc), where CUDA calls are not allowed.
  * The paper has no counterpart: this is an interface convenience only.
  *
  * Solves M11 X = B exactly as felbm_mass_solve does (same solver, same
@@ -336,6 +338,8 @@ int felbm_mass_solve(felbm_state* state, const double* B, double* X, int32_t k);
  * Enqueued on the state's stream; returns without synchronising.  The first
  * call on a device looks up the array's device address (once per device, with
  * that device made current); make that first call before any stream capture.
+ * The address is kept for the life of the process: the library must not be
+ * used across a cudaDeviceReset of that device.
  * Every call shares the one array of its device and leaves its contents
  * behind: calls that overlap on the GPU race, so serialise them (one stream,
  * or events).  They may overlap with felbm_step, which does not touch it. */

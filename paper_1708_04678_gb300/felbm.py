@@ -400,11 +400,35 @@ class State:
         _check(lib().felbm_mass_solve(self.handle, _ptr(B), _ptr(X), k))
         return X
 
-    def mass_solve_static(self, d_B, d_X, k=None):
+    def check_static_solve_args(self, d_B, d_X):
+        """Reject, before anything is launched, tensors that the C ABI would
+        read or write out of bounds: B and X must be contiguous float64
+        tensors of shape (k, n_nodes), 1 <= k <= 18, on the state's device,
+        and must not overlap.  Returns k."""
+        torch = self.torch
+        for name, t in (("B", d_B), ("X", d_X)):
+            if not isinstance(t, torch.Tensor):
+                raise ValueError(f"{name}: a torch tensor on the state's device is required")
+            if t.dtype != torch.float64:
+                raise ValueError(f"{name}: dtype must be float64, got {t.dtype}")
+            if not t.is_contiguous():
+                raise ValueError(f"{name}: must be contiguous")
+            if t.device != self.workspace.device:
+                raise ValueError(f"{name}: on {t.device}, the state lives on {self.workspace.device}")
+            if t.dim() != 2 or t.shape[1] != self.N or not 1 <= t.shape[0] <= 18:
+                raise ValueError(f"{name}: shape must be (k, {self.N}) with 1 <= k <= 18, got {tuple(t.shape)}")
+        if d_X.shape != d_B.shape:
+            raise ValueError(f"X has shape {tuple(d_X.shape)}, B has {tuple(d_B.shape)}")
+        nbytes = d_B.numel() * 8
+        if d_B.data_ptr() < d_X.data_ptr() + nbytes and d_X.data_ptr() < d_B.data_ptr() + nbytes:
+            raise ValueError("X overlaps B")
+        return int(d_B.shape[0])
+
+    def mass_solve_static(self, d_B, d_X):
         """felbm_mass_solve_static: device tensors B, X of shape (k, n_nodes),
         float64, caller order; enqueued on the state's stream."""
-        k = d_B.shape[0] if k is None else k
-        _check(lib().felbm_mass_solve_static(self.handle, d_B.data_ptr(), d_X.data_ptr(), int(k)))
+        k = self.check_static_solve_args(d_B, d_X)
+        _check(lib().felbm_mass_solve_static(self.handle, d_B.data_ptr(), d_X.data_ptr(), k))
 
     # -- adjoint and checkpoints ------------------------------------------
     def set_wetting(self, phi_c):

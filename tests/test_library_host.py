@@ -175,3 +175,36 @@ def test_channel_mesh_with_a_hole(lib):
     assert info["n_wall_edges"] == 2 * L + 2 * (2 * H)
     assert abs(info["total_area"] - (nx * ny - L * 2 * H)) < 1e-9
     assert info["n_groups"] == 1
+
+
+def test_static_solve_arguments_are_validated_before_any_launch():
+    """felbm_mass_solve_static reads and writes k x n_nodes doubles through
+    raw device pointers, so the binding rejects every tensor that would make
+    it run past a buffer -- wrong dtype, strides, shape, k, device, or X
+    overlapping B -- before the C ABI is called (the handle here is a dummy
+    that a call would dereference)."""
+    torch = pytest.importorskip("torch")
+    n = 40
+    st = F.State.__new__(F.State)
+    st.torch, st.N, st.handle = torch, n, None
+    st.workspace = torch.empty(16, dtype=torch.uint8)          # the state's device: cpu here
+    good = torch.zeros((3, n), dtype=torch.float64)
+    assert st.check_static_solve_args(good, torch.zeros_like(good)) == 3
+    bad_pairs = [
+        (good.float(), torch.zeros_like(good)),                               # dtype of B
+        (good, torch.zeros((3, n), dtype=torch.float32)),                     # dtype of X
+        (torch.zeros((n, 3), dtype=torch.float64).t(), torch.zeros_like(good)),  # strided B
+        (torch.zeros((3, n - 1), dtype=torch.float64), torch.zeros((3, n - 1), dtype=torch.float64)),
+        (torch.zeros((19, n), dtype=torch.float64), torch.zeros((19, n), dtype=torch.float64)),
+        (torch.zeros((0, n), dtype=torch.float64), torch.zeros((0, n), dtype=torch.float64)),
+        (torch.zeros(3 * n, dtype=torch.float64), torch.zeros(3 * n, dtype=torch.float64)),
+        (good, torch.zeros((2, n), dtype=torch.float64)),                     # X smaller than B
+        (good, good),                                                         # X aliases B
+        (good, torch.zeros((3, n), dtype=torch.float64, device="meta")),      # another device
+        (good.numpy(), torch.zeros_like(good)),                               # not a tensor
+    ]
+    buf = torch.zeros((4, n), dtype=torch.float64)
+    bad_pairs.append((buf[:3], buf[1:]))                                      # partial overlap
+    for B_, X_ in bad_pairs:
+        with pytest.raises(ValueError):
+            st.mass_solve_static(B_, X_)

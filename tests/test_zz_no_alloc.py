@@ -1,9 +1,9 @@
 """felbm_mass_solve_static: the mass solve for callers that cannot allocate.
 
 Some callers must not allocate device memory at the point where they solve
-(a host callback, a plugin whose host owns all device memory, a section that
-must not synchronise) and cannot lend the state's workspace because a time
-step may be using it.  The static entry point keeps its iterates in a
+(a plugin whose host application owns all device memory, a section that must
+not synchronise) and cannot lend the state's workspace because a time step
+may be using it.  The static entry point keeps its iterates in a
 library-owned static device array instead.  This file checks, through the C
 ABI, that it returns what the ordinary workspace-backed solve returns, on two
 calls in a row (the array keeps the previous call's contents), for a full and
