@@ -5,18 +5,27 @@
 
 A step is one full time step (collision, chemical potential with the wetting
 boundary, element Laplacian of mu, P0 forces, streaming right-hand side and
-the consistent-mass solve) of the 256x256 free droplet (131,585 grid points,
-131,072 unique nodes after periodic identification, 4 triangles per cell,
-jitter 0.25h, density ratio 100).  The metric is node-updates per second: one
-node, one step, both D2Q9 sets.  L2 is flushed before every timed step (a
-256 MiB write), each step is timed with CUDA events on the library's stream.
+the consistent-mass solve) of the rough-wall droplet: a 2048 x 1024 box whose
+bottom wall is y = 8 + 4 sin(2 pi x / 64), meshed body-fitted with 1017 rows
+(2,082,816 nodes, 4,161,536 triangles, jitter 0.2h), droplet R 300, contact
+angle 60 degrees, density ratio 100.  Its state and solve working set are far
+above the 129 MB L2, and L2 is flushed before every timed step (a 256 MiB
+write).  The metric is node-updates per second: one node, one step, both D2Q9
+sets; each step is timed with CUDA events on the library's stream.  The
+headline is the FP32-deviation form; the plain FP64 step of the same workload
+is timed beside it, and the 256 x 256 free droplet, the 64-droplet batch, the
+adjoint and the 3D step as further sections.
 
 The path has no exchange step across meshes, so N > 1 runs N independent
 replicas (one per GPU, weak scaling); value is the sum over ranks, the time
 the maximum over ranks.
 
 ``--impl reference`` times the FP64 CPU oracle (numpy/scipy, one host core)
-on full-size steps of the same workload, capped to about two minutes.
+on steps of a 128-column periodic strip of the same workload (130,176 nodes,
+the same rows, wall, jitter and physics), capped to about two minutes: one
+step of the full mesh takes the oracle over a minute and several GB, and
+runs slower per node-update than the strip does (more cache misses), so the
+strip's rate is an upper bound on the oracle's full-mesh rate.
 """
 from __future__ import annotations
 
@@ -56,24 +65,32 @@ def parse():
 
 def workload():
     from paper_1708_04678_gb300 import inputs as I
-    return I.free_droplet_256()
+    return I.rough_wall_droplet()
+
+
+def oracle_sample():
+    """The bounded sample of the workload the CPU oracle is timed on."""
+    from paper_1708_04678_gb300 import inputs as I
+    return I.rough_wall_strip()
 
 
 def workload_config(w, world=1):
     """The `config` object of both arms: what the workload is."""
-    return {"workload": "free droplet 256x256: 131,585 grid points (131,072 nodes), 4 triangles per cell, "
-                        "jitter 0.25h, density ratio 100, R 48, dt 0.05",
+    return {"workload": "rough-wall droplet 2048x1024: wall y = 8 + 4 sin(2 pi x/64), 1017 body-fitted rows "
+                        "(2,082,816 nodes, 4,161,536 triangles), jitter 0.2h, R 300, 60 deg, density ratio 100, "
+                        "dt 0.25",
             "nodes": len(w["mesh"]["xy"]), "triangles": len(w["mesh"]["tri"]), "dt": w["phys"]["dt"],
-            "l2": "flushed before every timed step (256 MiB write)",
+            "l2": "inputs larger than L2 (about 0.6 GB touched per solve step) and L2 flushed before every "
+                  "timed step (256 MiB write)",
             "parallelism": f"replicas x{world}"}
 
 
 # ------------------------------------------------------------- CPU oracle --
 def run_oracle(budget_s, max_steps, warmup):
-    """Time the FP64 oracle on full-size steps of the workload; returns
-    (node-updates/s, steps timed, seconds)."""
+    """Time the FP64 oracle on steps of the bounded sample of the workload;
+    returns (node-updates/s, steps timed, seconds)."""
     from oracle import OracleMesh, OracleSim, params_from_physical
-    w = workload()
+    w = oracle_sample()
     m = w["mesh"]
     sim = OracleSim(OracleMesh(m["xy"], m["tri"], m["wall_edges"], m["wall_id"], m["period"]),
                     params_from_physical(w["phys"]), w["C0"])
@@ -226,15 +243,15 @@ def phase_pass(st, torch, stream, flush, n):
     return phases
 
 
-def time_precision(F, torch, w, dev, precision, K, W, flush, barrier, world, dist):
+def time_precision(F, torch, w, dev, precision, K, W, flush, barrier, world, dist, e2e=True):
     """Build a state of the workload in one precision, run W warm-up steps and
     K timed steps (L2 flushed before each), then K end-to-end steps through
-    host buffers.  Returns the measurements of this rank."""
+    host buffers, in two forms.  Returns the measurements of this rank."""
     mesh = F.Mesh.from_dict(w["mesh"])
     prm = F.params_derive(w["phys"], precision=precision)
     stream = torch.cuda.Stream(dev)
     st = F.State(mesh, prm, w["C0"], device=dev, stream=stream)
-    tune = st.autotune(trials=5)
+    tune = st.autotune(trials=3)
     for k in range(W):
         with torch.cuda.stream(stream):
             flush.fill_(k & 255)
@@ -258,37 +275,53 @@ def time_precision(F, torch, w, dev, precision, K, W, flush, barrier, world, dis
     # phase split (and the solve sweep's launch time) from a separate pass with phase events
     phases = phase_pass(st, torch, stream, flush, min(K, 10))
     diag = st.diagnostics(w["centre"], w["R"], w["phys"]["xi"])
-
-    # end to end through the public API with host buffers, every step: the
-    # pinned g, h copied in (set_state copies on its own stream, so the copy
-    # overlaps the previous step), one step, and the step's diagnostics read
-    # back asynchronously into pinned slots; all K results are read and
-    # finished on the host inside the timed region
-    g0, h0 = st.get_state()
-    gp = torch.from_numpy(g0).pin_memory()
-    hp = torch.from_numpy(h0).pin_memory()
-    slots = torch.zeros((K, F.DIAG_SLOTS), dtype=torch.float64).pin_memory()
-    for k in range(2):
-        st.set_state(gp, hp)
-        st.step(1)
-        st.diagnostics_enqueue(slots[k])
-    torch.cuda.synchronize()
-    barrier()
-    t0 = time.perf_counter()
-    for k in range(K):
-        st.set_state(gp, hp)
-        st.step(1)
-        st.diagnostics_enqueue(slots[k])
-    stream.synchronize()
-    e2e_diag = [st.diag_finish(slots[k]) for k in range(K)]
-    e2e_s = max_over_ranks(time.perf_counter() - t0, torch, dist, world, dev)
-    if any(d["status"] != 0 for d in e2e_diag):
-        raise RuntimeError("end-to-end steps produced a non-finite state")
-    ph = {k: statistics.mean(p[k] for p in phases) for k in phases[0] if k.endswith("_ms")}
-    info = mesh.info()
+    out = {"total_ms": total_ms, "tune": tune, "diag": diag,
+           "phase_ms": {k: statistics.mean(p[k] for p in phases) for k in phases[0] if k.endswith("_ms")},
+           "launches": phases[0]["launches"], "solve_launches": phases[0]["solve_launches"]}
+    if e2e:
+        # end to end through the public API with host buffers, every step: the
+        # pinned g, h copied in (set_state copies on its own stream, so the
+        # copy overlaps the previous step), one step, and the step's
+        # diagnostics read back asynchronously into pinned slots; all K
+        # results are read and finished on the host inside the timed region
+        g0, h0 = st.get_state()
+        gp = torch.from_numpy(g0).pin_memory()
+        hp = torch.from_numpy(h0).pin_memory()
+        slots = torch.zeros((K, F.DIAG_SLOTS), dtype=torch.float64).pin_memory()
+        for k in range(2):
+            st.set_state(gp, hp)
+            st.step(1)
+            st.diagnostics_enqueue(slots[k])
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        for k in range(K):
+            st.set_state(gp, hp)
+            st.step(1)
+            st.diagnostics_enqueue(slots[k])
+        stream.synchronize()
+        e2e_diag = [st.diag_finish(slots[k]) for k in range(K)]
+        out["e2e_s"] = max_over_ranks(time.perf_counter() - t0, torch, dist, world, dev)
+        if any(d["status"] != 0 for d in e2e_diag):
+            raise RuntimeError("end-to-end steps produced a non-finite state")
+        # the same with the whole state read back every step (felbm_get_state
+        # into pinned host arrays, which synchronises) instead of the metrics
+        go = torch.empty_like(gp).pin_memory()
+        ho = torch.empty_like(hp).pin_memory()
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        for k in range(K):
+            st.set_state(gp, hp)
+            st.step(1)
+            st.get_state(go.numpy(), ho.numpy())
+        out["e2e_state_s"] = max_over_ranks(time.perf_counter() - t0, torch, dist, world, dev)
+        if not (np.isfinite(go.numpy()).all() and np.isfinite(ho.numpy()).all()):
+            raise RuntimeError("end-to-end steps produced a non-finite state")
+        out["state_bytes"] = int(gp.numel() * 8 + hp.numel() * 8)
+    out["info"] = mesh.info()
     st.close()
-    return {"total_ms": total_ms, "e2e_s": e2e_s, "phase_ms": ph, "launches": phases[0]["launches"], "tune": tune,
-            "solve_launches": phases[0]["solve_launches"], "info": info, "diag": diag}
+    return out
 
 
 def time_batch(F, torch, dev, K, flush, barrier, world, dist):
@@ -362,40 +395,22 @@ def time_adjoint(F, torch, dev, K):
             "adjoint_node_updates_per_s": n / (adj_ms * 1e-3), "adjoint_over_forward": adj_ms / fwd_ms}
 
 
-def time_large(F, torch, dev, K, flush):
-    """FP32-deviation steps of the 2048x1024 rough-wall droplet (2,082,816
-    nodes; state and solve working set far above L2): time per step and the
-    solve sweep's algorithmic bandwidth."""
+def time_free_droplet(F, torch, dev, K, flush, barrier, world, dist):
+    """The 256 x 256 free droplet (131,072 nodes, 4 triangles per cell, jitter
+    0.25h, density ratio 100, dt 0.05): FP32-deviation and FP64 steps.  Its
+    solve working set fits in L2 inside a step."""
     from paper_1708_04678_gb300 import inputs as I
-    w = I.rough_wall_droplet()
-    mesh = F.Mesh.from_dict(w["mesh"])
-    stream = torch.cuda.Stream(dev)
-    st = F.State(mesh, F.params_derive(w["phys"], precision=F.FP32_DEV), w["C0"], device=dev, stream=stream)
-    tune = st.autotune(trials=2)
-    for k in range(2):
-        st.step(1)
-    tot = 0.0
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    for k in range(K):
-        with torch.cuda.stream(stream):
-            flush.fill_(k & 255)
-        e0.record(stream)
-        st.step(1)
-        e1.record(stream)
-        e1.synchronize()
-        tot += e0.elapsed_time(e1)
-    phases = phase_pass(st, torch, stream, flush, min(K, 5))
+    w = I.free_droplet_256()
     n = len(w["mesh"]["xy"])
-    info = mesh.info()
-    solve = statistics.mean(p["solve_ms"] for p in phases)
-    sweep_ms = solve / phases[0]["solve_launches"]
-    alg = n * 4 * 18 * 4 + info["nnz"] * (4 + 4) + n * (4 + 4)   # as for the main roofline line
-    d = st.diagnostics(w["centre"], w["R"], 4.0, 0)
-    st.close()
-    return {"workload": "rough-wall droplet 2048x1024 (2,082,816 nodes), FP32 deviation storage",
-            "steps": K, "ms_per_step": tot / K, "value": n * K / (tot * 1e-3), "unit": "node-updates/s",
-            "sweep_ms": sweep_ms, "sweep_alg_GBps": alg / (sweep_ms * 1e-3) / 1e9, "autotune": tune,
-            "finite": d["status"] == 0}
+    out = {"workload": "free droplet 256x256 (131,072 nodes, 262,144 triangles), R 48, density ratio 100, dt 0.05"}
+    for name, prec in (("fp32_dev", F.FP32_DEV), ("fp64", F.FP64)):
+        r = time_precision(F, torch, w, dev, prec, K, 3, flush, barrier, world, dist, e2e=False)
+        out[name] = {"value": job_rate(n, K, world, r["total_ms"]), "unit": "node-updates/s",
+                     "ms_per_step": r["total_ms"] / K, "steps": K,
+                     "phase_ms": {k: round(v, 5) for k, v in r["phase_ms"].items()},
+                     "sweep_ms": r["phase_ms"]["solve_ms"] / r["solve_launches"], "autotune": r["tune"],
+                     "finite": r["diag"]["status"] == 0}
+    return out
 
 
 def time_3d(torch, dev, K, flush):
@@ -510,30 +525,32 @@ def run_gpu(args):
     with ClockSampler(local) as clk:
         r32 = time_precision(F, torch, w, dev, F.FP32_DEV, K, W, flush, barrier, world, dist)
         r64 = time_precision(F, torch, w, dev, F.FP64, K, W, flush, barrier, world, dist)
-        rb = None if args.no_batch else time_batch(F, torch, dev, max(3, K // 5), flush, barrier, world, dist)
-        radj = None if args.no_batch else time_adjoint(F, torch, dev, max(5, K // 2))
-        rl = None if args.no_batch else time_large(F, torch, dev, max(3, K // 10), flush)
-        r3 = None if args.no_batch else time_3d(torch, dev, max(5, K // 5), flush)
+        extra = not args.no_batch
+        rfd = time_free_droplet(F, torch, dev, K, flush, barrier, world, dist) if extra else None
+        rb = time_batch(F, torch, dev, max(10, K // 2), flush, barrier, world, dist) if extra else None
+        radj = time_adjoint(F, torch, dev, max(5, K // 2)) if extra else None
+        r3 = time_3d(torch, dev, max(5, K // 5), flush) if extra else None
 
     for name, r in (("FP32", r32), ("FP64", r64)):
         if r["diag"]["status"] != 0:
             raise SystemExit(f"bench: the {name} state is not finite after the timed steps")
     if rank == 0:
         nnz = r32["info"]["nnz"]
-        # dominant kernel of the FP32-deviation step: one FP32 Chebyshev sweep
-        # of the 18-RHS mass solve (the last sweep also updates the fields)
+        # dominant kernel of the FP32-deviation step: one step of the FP32
+        # solve of the 18 right-hand sides (the last one also updates the
+        # fields), timed as the solve phase over its launches
         sweep_ms = r32["phase_ms"]["solve_ms"] / r32["solve_launches"]
-        # algorithmic bytes of one sweep: gathered x_k, own x_{k-1}, rhs, new
-        # x (4 x 18 floats per node), the mass row (column index + FP32 value
-        # per entry), row pointer and inverse lumped mass per node
-        alg_bytes = N * 4 * 18 * 4 + nnz * (4 + 4) + N * (4 + 4)
+        # algorithmic bytes of one solve step x_{k+1} = x_k + tau m^-1 (b - M x_k):
+        # gathered x_k, b and the new x (3 x 18 floats per node), the mass
+        # row (column index + FP32 value per entry), the inverse lumped mass
+        alg_bytes = N * (3 * 18 * 4 + 4) + nnz * (4 + 4)
         hbm_peak, peak_src = peaks()
         achieved = alg_bytes / (sweep_ms * 1e-3) / 1e9
         # whole step, with the minimum bytes per node-update of the FP32 form:
         # distributions read and written (2 x 18 x 4), right-hand side written
-        # and read (2 x 18 x 4), per Chebyshev sweep a gathered iterate, the
-        # residual and the new iterate (3 x 18 x 4), about 200 B of nodal and
-        # element fields
+        # and read (2 x 18 x 4), per solve step a gathered iterate, the
+        # right-hand side and the new iterate (3 x 18 x 4), about 200 B of
+        # nodal and element fields
         k_sweeps = r32["solve_launches"] + 1
         step_bytes = 2 * 18 * 4 + 2 * 18 * 4 + k_sweeps * 3 * 18 * 4 + 200
 
@@ -542,10 +559,14 @@ def run_gpu(args):
                     "dtype": dtype, "phase_ms": {k: round(v, 5) for k, v in r["phase_ms"].items()},
                     "launches_per_step": r["launches"], "autotune": r["tune"],
                     "e2e_value": job_rate(N, K, world, r["e2e_s"] * 1e3),
+                    "e2e_state_out_value": job_rate(N, K, world, r["e2e_state_s"] * 1e3),
                     "after_timed_steps": {k: r["diag"][k] for k in ("max_u", "delta_p", "mass_drift_rel",
-                                                                    "interface_rho_uu", "status")}}
+                                                                    "wetted_length", "theta_deg", "status")}}
 
         s32, s64 = summary(r32, "f32 (FP64 C, mu, reductions)"), summary(r64, "f64")
+        s64["e2e"] = {"value": s64["e2e_value"], "unit": "node-updates/s", "h2d_bytes_per_step": r64["state_bytes"],
+                      "d2h_bytes_per_step": 8 * F.DIAG_SLOTS}
+        nominal = 8000.0
         out = {
             "metric": METRIC,
             "value": s32["value"],
@@ -560,24 +581,28 @@ def run_gpu(args):
             "dtype": "f32",
             "data": "synthetic",
             "config": dict(workload_config(w, world), precision="FP32 deviation storage (fp32_dev); "
-                           "plain FP64 in fp64", solver=f"FP32 Chebyshev, {r32['solve_launches'] + 1} sweeps"),
+                           "plain FP64 in fp64", solver=f"FP32 Richardson steps at the Chebyshev roots, "
+                                                         f"{r32['solve_launches'] + 1} per step"),
             "fp32_dev": s32,
             "fp64": s64,
+            "free_droplet_256": rfd,
             "batched": rb,
             "adjoint": radj,
-            "large_mesh": rl,
             "tetrahedra_3d": r3,
             "step_roofline": {"alg_bytes_per_node_update": step_bytes, "sweeps": k_sweeps,
                               "achieved": s32["value"] * step_bytes / 1e9, "peak": hbm_peak, "unit": "GB/s",
-                              "frac": s32["value"] * step_bytes / 1e9 / hbm_peak},
+                              "frac": s32["value"] * step_bytes / 1e9 / hbm_peak,
+                              "frac_of_nominal_8TBps": s32["value"] * step_bytes / 1e9 / nominal},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                          "frac": achieved / hbm_peak, "traffic": recorded_traffic("k_sweep32"),
-                         "kernel": "k_sweep32 (one FP32 Chebyshev sweep of the 18-RHS mass solve)",
+                         "kernel": "k_sweep32 (one step of the FP32 solve of the 18 right-hand sides)",
                          "source_hash": source_hash(),
                          "alg_bytes_per_launch": alg_bytes, "launch_ms": sweep_ms,
-                         "peak_source": peak_src},
+                         "peak_source": peak_src, "frac_of_nominal_8TBps": achieved / nominal},
             "e2e": {"value": s32["e2e_value"], "unit": "node-updates/s",
-                    "h2d_bytes_per_step": 2 * 9 * N * 8, "d2h_bytes_per_step": 8 * F.DIAG_SLOTS},
+                    "h2d_bytes_per_step": r32["state_bytes"], "d2h_bytes_per_step": 8 * F.DIAG_SLOTS},
+            "e2e_state_out": {"value": s32["e2e_state_out_value"], "unit": "node-updates/s",
+                              "h2d_bytes_per_step": r32["state_bytes"], "d2h_bytes_per_step": r32["state_bytes"]},
             "gpu_launches": r32["launches"] * K,
             "clocks": clk.summary(),
         }
@@ -597,8 +622,9 @@ def run_reference(args):
     warm = min(args.warmup, 1)
     v, n, secs = run_oracle(budget, args.steps, warm)
     why = "the requested steps" if n >= args.steps else f"the first step past {budget:.0f} s"
-    sample = (f"{n} full-size steps (after {warm} warm-up) of the 131,072-node free droplet in {secs:.1f} s "
-              f"(stopped after {why}); FP64 numpy/scipy oracle, one host core")
+    sample = (f"{n} steps (after {warm} warm-up) of the 128-column strip of the rough-wall droplet "
+              f"(130,176 nodes, the same rows, wall, jitter and physics) in {secs:.1f} s (stopped after {why}); "
+              f"FP64 numpy/scipy oracle, one host core")
     out = {"metric": METRIC, "value": v, "unit": "node-updates/s", "n_gpus": world, "steps": n,
            "warmup": warm, "ms_per_step": secs * 1e3 / n, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -615,8 +641,9 @@ def main():
     if args.cpu_baseline_only:
         v, n, secs = run_oracle(args.cpu_seconds, 10 ** 6, 1)
         print(json.dumps({"value": v, "unit": "node-updates/s", "cores": 1, "kind": "oracle",
-                          "sample": f"{n} full-size steps of the 131,072-node free droplet after 1 warm-up, "
-                                    f"{secs:.1f} s, numpy/scipy single thread"}))
+                          "sample": f"{n} steps of the 128-column strip of the rough-wall droplet (130,176 "
+                                    f"nodes, the same rows, wall, jitter and physics) after 1 warm-up, {secs:.1f} s, "
+                                    f"numpy/scipy single thread"}))
         return
     if args.impl == "reference":
         run_reference(args)

@@ -62,8 +62,10 @@ extern "C" {
 #define FELBM_FP32_DEV 1
 
 /* Consistent-mass solve (Sec. II.C: M11 with the lumped-mass preconditioner).
- * MIXED: iterative refinement -- FP32 Chebyshev corrections, residual carried
- *        in FP64 (default; reaches FP64 round-off with solver_rounds = 3).
+ * MIXED: iterative refinement -- FP32 corrections (Richardson steps at the
+ *        reciprocal Chebyshev roots of the spectrum [1/4, 1], which give the
+ *        Chebyshev error bound), residual carried in FP64 (default; reaches
+ *        FP64 round-off with solver_rounds = 3).
  * FP64:  Chebyshev sweeps in FP64 throughout. */
 #define FELBM_SOLVER_MIXED 0
 #define FELBM_SOLVER_FP64 1
@@ -91,9 +93,9 @@ extern "C" {
  *  lap_mode        FELBM_LAP_CONSISTENT or FELBM_LAP_PAPER
  *  precision       FELBM_FP64 or FELBM_FP32_DEV
  *  solver_mode     FELBM_SOLVER_MIXED or FELBM_SOLVER_FP64
- *  solver_iters    Chebyshev sweeps per correction (MIXED, 0 = 14, error
- *                  bound 2*3^-14 per correction) or in total (FP64, 0 = 32,
- *                  bound 2*3^-32); >= 2
+ *  solver_iters    sweeps per correction (MIXED, 0 = 14, error
+ *                  bound 2*3^-14 per correction; FP32_DEV, 0 = 10, bound
+ *                  2*3^-10) or in total (FP64, 0 = 32, bound 2*3^-32); >= 2
  *  solver_rounds   corrections of the MIXED solve (0 = 3 for FP64 storage,
  *                  1 for FP32_DEV)
  *  lapmu_mode      FELBM_LAPMU_FACE (default) or FELBM_LAPMU_NODAL          */

@@ -355,11 +355,13 @@ __global__ void __launch_bounds__(128) k_element(DevMesh m, Phys c, Bufs b) {
 // RHS_{i,a} = sum_{T at i} R_{T,a} (dt/3 + dt^2/2 e_a.b_{i,T})
 //           - dt sum_{wall e at i} (e_a.n) [L/3 (psi_opp - psi)_i + L/6 (psi_opp - psi)_o]
 // (second sum only for incoming directions e_a.n < 0; o = other end of e).
-// Also writes the first Chebyshev iterate x1 = RHS / (m_i theta): in FP64
-// (FP64 Chebyshev) or, for the mixed-precision solve, in FP32 together with
-// the FP32 copy of the right-hand side.
+// Also writes the first iterate of the solve x1 = first_scale * RHS / m_i
+// (first_scale = 1/theta for the FP64 Chebyshev recurrence, tau_0 for the
+// FP32 Richardson steps): in FP64 (FP64 Chebyshev) or, for the
+// mixed-precision solve, in FP32 together with the FP32 copy of the
+// right-hand side.
 template <bool kMixed>
-__global__ void __launch_bounds__(128) k_rhs(DevMesh m, Phys c, Bufs b, double inv_theta) {
+__global__ void __launch_bounds__(128) k_rhs(DevMesh m, Phys c, Bufs b, double first_scale) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= m.N) return;
     const int Np = m.Np;
@@ -409,7 +411,7 @@ __global__ void __launch_bounds__(128) k_rhs(DevMesh m, Phys c, Bufs b, double i
         FELBM_WALL_Q(5) FELBM_WALL_Q(6) FELBM_WALL_Q(7) FELBM_WALL_Q(8)
 #undef FELBM_WALL_Q
     }
-    double s = m.inv_lumped[i] * inv_theta;
+    double s = m.inv_lumped[i] * first_scale;
 #pragma unroll
     for (int q = 0; q < 18; ++q) {
         b.rhs[q * Np + i] = acc[q];
@@ -422,13 +424,14 @@ __global__ void __launch_bounds__(128) k_rhs(DevMesh m, Phys c, Bufs b, double i
     }
 }
 
-// First Chebyshev iterate for a standalone solve: x1 = B / (m_i theta).
+// First iterate for a standalone solve: x1 = first_scale * B / m_i
+// (1/theta for the FP64 recurrence, tau_0 for the FP32 steps).
 template <bool kMixed>
-__global__ void __launch_bounds__(kBlock) k_cheb_start(DevMesh m, Bufs b, double inv_theta) {
+__global__ void __launch_bounds__(kBlock) k_cheb_start(DevMesh m, Bufs b, double first_scale) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= m.N) return;
     const int Np = m.Np;
-    double s = m.inv_lumped[i] * inv_theta;
+    double s = m.inv_lumped[i] * first_scale;
 #pragma unroll
     for (int q = 0; q < 18; ++q) {
         double r = b.rhs[q * Np + i];
@@ -492,9 +495,18 @@ __device__ __forceinline__ void pdl_release() { asm volatile("griddepcontrol.lau
 #include "felbm_dev32.cuh"
 #include "felbm_adjoint.cuh"
 
+// One step of the FP32 correction solve (CSR rows): Richardson iteration
+// x_{k+1} = x_k + tau_k m^{-1} (b - M x_k) with the Chebyshev step sizes
+// tau_k = 1 / lambda_k, lambda_k the roots of the degree-K Chebyshev
+// polynomial on the spectrum [1/4, 1] of m^{-1} M11 (taken smallest and
+// largest alternately, which keeps every partial product below 1 and the
+// round-off amplification below 3).  After K steps from x_0 = 0 the error
+// polynomial is the same scaled Chebyshev polynomial as for the three-term
+// recurrence, but each step reads only x_k (gathered) and b.
+//   cur = x_k; the new iterate goes to nxt (or to the final destination).
 template <int kFinal>
 __global__ void __launch_bounds__(128) k_cheb32(DevMesh m, Phys c, Bufs b, const float* __restrict__ cur,
-                                                float* prev, float a, float cc, int first, int have_x64) {
+                                                float* nxt, float tau, int have_x64) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= m.N) return;
     const int Np = m.Np;
@@ -507,15 +519,14 @@ __global__ void __launch_bounds__(128) k_cheb32(DevMesh m, Phys c, Bufs b, const
 #pragma unroll
         for (int q = 0; q < 18; ++q) acc[q] = fmaf(mv, cur[q * Np + j], acc[q]);
     }
-    float s = cc * m.inv_lumped32[i];
+    float s = tau * m.inv_lumped32[i];
     float d[18];
 #pragma unroll
     for (int q = 0; q < 18; ++q) {
         float xk = cur[q * Np + i];
-        float xm = first ? 0.0f : prev[q * Np + i];
-        float xn = xk + a * (xk - xm) + s * (b.r32[q * Np + i] - acc[q]);
+        float xn = xk + s * (b.r32[q * Np + i] - acc[q]);
         if (kFinal == kStore) {
-            prev[q * Np + i] = xn;
+            nxt[q * Np + i] = xn;
         } else if (kFinal == kUpdateDev) {
             d[q] = xn;
         } else {
@@ -534,22 +545,25 @@ __global__ void __launch_bounds__(128) k_cheb32(DevMesh m, Phys c, Bufs b, const
 // the predecessor's results before touching them.  Both instructions are
 // no-ops for a kernel launched without the attribute.
 
-// The FP32 sweep of k_cheb32 on the ELL copy of the pattern (kW entries per
+// The FP32 step of k_cheb32 on the ELL copy of the pattern (kW entries per
 // row, padded with the own column and value 0).  Row indices and values are
-// loaded up front (coalesced, column-major); for the store variant the g and
-// h halves of a node run in two threads (blockIdx.y), doubling the threads in
-// flight for this latency-bound gather.
-// kParts threads per node (blockIdx.y picks the part), each owning 18/kParts
-// of the node's rows; the field update needs all 18 in one thread.
+// loaded up front (coalesced, column-major).
+// kParts threads per node, each owning 18/kParts of the node's rows (more
+// threads in flight for this latency-bound gather); the field update needs
+// all 18 in one thread.  The parts of one node block are consecutive blocks
+// (blockIdx.x = kParts * node block + part), so they run together and share
+// the block's matrix rows through L2 instead of fetching them from DRAM
+// once per part.
 template <int kFinal, int kW, int kParts>
 __global__ void __launch_bounds__(128) k_sweep32(DevMesh m, Phys c, Bufs b, const float* __restrict__ cur,
-                                                 float* prev, float a, float cc, int first, int have_x64) {
+                                                 float* nxt, float tau, int have_x64) {
     pdl_release();
     static_assert(kFinal != kUpdateDev || kParts == 1, "the field update needs the whole node");
     static_assert(18 % kParts == 0, "parts must divide 18");
     constexpr int NQ = 18 / kParts;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const int q0 = NQ * (int)blockIdx.y;
+    const int nb = (int)blockIdx.x / kParts;
+    const int i = nb * (int)blockDim.x + (int)threadIdx.x;
+    const int q0 = NQ * ((int)blockIdx.x - nb * kParts);
     const int Np = m.Np;
     int col[kW];
     float val[kW];
@@ -560,7 +574,7 @@ __global__ void __launch_bounds__(128) k_sweep32(DevMesh m, Phys c, Bufs b, cons
             val[k] = m.ell_val[k * Np + i];
         }
     }
-    const float s = cc * (i < m.N ? m.inv_lumped32[i] : 0.0f);
+    const float s = tau * (i < m.N ? m.inv_lumped32[i] : 0.0f);
     pdl_wait();
     if (i >= m.N) return;
     float acc[NQ];
@@ -576,10 +590,9 @@ __global__ void __launch_bounds__(128) k_sweep32(DevMesh m, Phys c, Bufs b, cons
     for (int q = 0; q < NQ; ++q) {
         const int r = (q0 + q) * Np + i;
         float xk = cur[r];
-        float xm = first ? 0.0f : prev[r];
-        float xn = xk + a * (xk - xm) + s * (b.r32[r] - acc[q]);
+        float xn = xk + s * (b.r32[r] - acc[q]);
         if (kFinal == kStore) {
-            prev[r] = xn;
+            nxt[r] = xn;
         } else if (kFinal == kUpdateDev) {
             d[q] = xn;
         } else {
@@ -594,9 +607,9 @@ __global__ void __launch_bounds__(128) k_sweep32(DevMesh m, Phys c, Bufs b, cons
 }
 
 // x <- x + e ; rho <- rho - M11 e (FP64) ; FP32 copy of rho and the first
-// Chebyshev iterate of the next correction, rho / (m theta).
+// iterate of the next correction, tau_0 rho / m.
 __global__ void __launch_bounds__(128) k_refine(DevMesh m, Bufs b, const float* __restrict__ e,
-                                                float* next_first, int first_round, double inv_theta) {
+                                                float* next_first, int first_round, double tau0) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= m.N) return;
     const int Np = m.Np;
@@ -609,7 +622,7 @@ __global__ void __launch_bounds__(128) k_refine(DevMesh m, Bufs b, const float* 
 #pragma unroll
         for (int q = 0; q < 18; ++q) acc[q] += mv * (double)e[q * Np + j];
     }
-    double s = m.inv_lumped[i] * inv_theta;
+    double s = m.inv_lumped[i] * tau0;
 #pragma unroll
     for (int q = 0; q < 18; ++q) {
         double xo = first_round ? 0.0 : b.x64[q * Np + i];
@@ -936,13 +949,11 @@ __global__ void __launch_bounds__(kBlock) k_diag_fused32(DevMesh m, Phys c, Bufs
 constexpr int kCtaThreads = 512;
 constexpr int kMaxSweeps = 64;
 struct ChebCoef {
-    float a[kMaxSweeps];
-    float c[kMaxSweeps];
+    float tau[kMaxSweeps];   // Richardson step sizes of the FP32 solve (see k_cheb32)
 };
 
 __device__ __forceinline__ void sweep32_node(const DevMesh& m, const Phys& c, const Bufs& b, int i,
-                                             const float* cur, float* prev, float a, float cc, int first,
-                                             bool update) {
+                                             const float* cur, float* nxt, float tau, bool update) {
     const int Np = m.Np;
     float acc[18];
 #pragma unroll
@@ -962,24 +973,23 @@ __device__ __forceinline__ void sweep32_node(const DevMesh& m, const Phys& c, co
             for (int q = 0; q < 18; ++q) acc[q] = fmaf(v, cur[q * Np + j], acc[q]);
         }
     }
-    const float s = cc * m.inv_lumped32[i];
+    const float s = tau * m.inv_lumped32[i];
     float d[18];
 #pragma unroll
     for (int q = 0; q < 18; ++q) {
         float xk = cur[q * Np + i];
-        float xm = first ? 0.0f : prev[q * Np + i];
-        float xn = xk + a * (xk - xm) + s * (b.r32[q * Np + i] - acc[q]);
+        float xn = xk + s * (b.r32[q * Np + i] - acc[q]);
         if (update)
             d[q] = xn;
         else
-            prev[q * Np + i] = xn;
+            nxt[q * Np + i] = xn;
     }
     if (update) dev32_update(m, c, b, i, d);
 }
 
 __global__ void __launch_bounds__(kCtaThreads, 1) k_step_cta32(DevMesh m, Phys c, Bufs b, GroupTables gt,
                                                                const int32_t* __restrict__ groups, ChebCoef cf,
-                                                               int sweeps, float inv_theta) {
+                                                               int sweeps, float tau0) {
     const int g = groups[blockIdx.x];
     const int n0 = gt.node_begin[g], n1 = gt.node_end[g], t0 = gt.tri_begin[g], t1 = gt.tri_end[g];
     const int tid = threadIdx.x, nt = blockDim.x;
@@ -992,13 +1002,13 @@ __global__ void __launch_bounds__(kCtaThreads, 1) k_step_cta32(DevMesh m, Phys c
     __syncthreads();
     for (int t = t0 + tid; t < t1; t += nt) element32_tri(m, c, b, t);
     __syncthreads();
-    for (int i = n0 + tid; i < n1; i += nt) rhs32_node(m, c, b, i, inv_theta);
+    for (int i = n0 + tid; i < n1; i += nt) rhs32_node(m, c, b, i, tau0);
     __syncthreads();
     float* cur = b.e1;
     float* prv = b.e0;
     for (int k = 1; k < sweeps; ++k) {
         const bool last = k == sweeps - 1;
-        for (int i = n0 + tid; i < n1; i += nt) sweep32_node(m, c, b, i, cur, prv, cf.a[k], cf.c[k], k == 1, last);
+        for (int i = n0 + tid; i < n1; i += nt) sweep32_node(m, c, b, i, cur, prv, cf.tau[k], last);
         __syncthreads();
         float* tmp = cur;
         cur = prv;
@@ -1050,8 +1060,9 @@ struct felbm_state {
     int mode = FELBM_SOLVER_MIXED;
     int sweeps = 14;   // per correction (mixed) or in total (FP64)
     int rounds = 3;    // corrections of the mixed solve
-    std::vector<double> cheb_a, cheb_c;
-    double inv_theta = 1.0;
+    std::vector<double> cheb_a, cheb_c;   // three-term recurrence of the FP64 solve
+    double inv_theta = 1.0;               // its first iterate x_1 = m^{-1} b / theta
+    std::vector<double> tau;              // Richardson step sizes of the FP32 solves; tau[0] gives x_1
     int64_t step = 0;
     double mass0 = 0.0;
     int device = 0;
@@ -1281,50 +1292,47 @@ static void launch_k(bool pdl, void (*kern)(KArgs...), dim3 grid, dim3 block, cu
 // parts: threads per node for the store sweeps (1, 2, 3 or 6; autotuned).
 template <int kFinal, int kW>
 static void launch_sweep_w(felbm_state* st, const DevMesh& m, const Bufs& b, cudaStream_t s, const float* cur,
-                           float* prv, float a, float c, int first, int have_x64, bool pdl) {
+                           float* nxt, float tau, int have_x64, bool pdl) {
     const dim3 block(128);
     const int parts = kFinal == kUpdateDev ? 1 : st->sweep_parts;
-    const dim3 grid(grid_for(m.N, 128), parts);
+    const dim3 grid(grid_for(m.N, 128) * parts);
     switch (parts) {
         case 1:
-            launch_k(pdl, k_sweep32<kFinal, kW, 1>, grid, block, s, m, st->phys, b, cur, prv, a, c, first, have_x64);
+            launch_k(pdl, k_sweep32<kFinal, kW, 1>, grid, block, s, m, st->phys, b, cur, nxt, tau, have_x64);
             break;
         case 3:
             if constexpr (kFinal != kUpdateDev)
-                launch_k(pdl, k_sweep32<kFinal, kW, 3>, grid, block, s, m, st->phys, b, cur, prv, a, c, first,
-                         have_x64);
+                launch_k(pdl, k_sweep32<kFinal, kW, 3>, grid, block, s, m, st->phys, b, cur, nxt, tau, have_x64);
             break;
         case 6:
             if constexpr (kFinal != kUpdateDev)
-                launch_k(pdl, k_sweep32<kFinal, kW, 6>, grid, block, s, m, st->phys, b, cur, prv, a, c, first,
-                         have_x64);
+                launch_k(pdl, k_sweep32<kFinal, kW, 6>, grid, block, s, m, st->phys, b, cur, nxt, tau, have_x64);
             break;
         default:
             if constexpr (kFinal != kUpdateDev)
-                launch_k(pdl, k_sweep32<kFinal, kW, 2>, grid, block, s, m, st->phys, b, cur, prv, a, c, first,
-                         have_x64);
+                launch_k(pdl, k_sweep32<kFinal, kW, 2>, grid, block, s, m, st->phys, b, cur, nxt, tau, have_x64);
     }
 }
 
 template <int kFinal>
 static void launch_sweep(felbm_state* st, const DevMesh& m, const Bufs& b, cudaStream_t s, const float* cur,
-                         float* prv, float a, float c, int first, int have_x64, bool pdl) {
+                         float* nxt, float tau, int have_x64, bool pdl) {
     pdl = pdl && st->use_pdl;
     switch (m.ell_w) {
         case 7:
-            launch_sweep_w<kFinal, 7>(st, m, b, s, cur, prv, a, c, first, have_x64, pdl);
+            launch_sweep_w<kFinal, 7>(st, m, b, s, cur, nxt, tau, have_x64, pdl);
             break;
         case 9:
-            launch_sweep_w<kFinal, 9>(st, m, b, s, cur, prv, a, c, first, have_x64, pdl);
+            launch_sweep_w<kFinal, 9>(st, m, b, s, cur, nxt, tau, have_x64, pdl);
             break;
         case 12:
-            launch_sweep_w<kFinal, 12>(st, m, b, s, cur, prv, a, c, first, have_x64, pdl);
+            launch_sweep_w<kFinal, 12>(st, m, b, s, cur, nxt, tau, have_x64, pdl);
             break;
         case 16:
-            launch_sweep_w<kFinal, 16>(st, m, b, s, cur, prv, a, c, first, have_x64, pdl);
+            launch_sweep_w<kFinal, 16>(st, m, b, s, cur, nxt, tau, have_x64, pdl);
             break;
         default:
-            k_cheb32<kFinal><<<grid_for(m.N, 128), 128, 0, s>>>(m, st->phys, b, cur, prv, a, c, first, have_x64);
+            k_cheb32<kFinal><<<grid_for(m.N, 128), 128, 0, s>>>(m, st->phys, b, cur, nxt, tau, have_x64);
     }
 }
 
@@ -1354,22 +1362,22 @@ static const double* enqueue_solve(felbm_state* st, const DevMesh& m, const Bufs
         float* cur = A;
         float* prv = B;
         for (int k = 1; k < st->sweeps; ++k) {
-            const float a = (float)st->cheb_a[k], c = (float)st->cheb_c[k];
+            const float tau = (float)st->tau[k];
             const bool last = r == st->rounds - 1 && k == st->sweeps - 1;
             // the previous launch is a sweep of this round, or a kernel that released its dependents
             const bool pdl = k > 1 || (k == 1 && r == 0 && after_release);
             if (!last)
-                launch_sweep<kStore>(st, m, b, s, cur, prv, a, c, k == 1, have_x64, pdl);
+                launch_sweep<kStore>(st, m, b, s, cur, prv, tau, have_x64, pdl);
             else if (!into_psi)
-                launch_sweep<kAddX64>(st, m, b, s, cur, prv, a, c, k == 1, have_x64, pdl);
+                launch_sweep<kAddX64>(st, m, b, s, cur, prv, tau, have_x64, pdl);
             else if (st->dev32)
-                launch_sweep<kUpdateDev>(st, m, b, s, cur, prv, a, c, k == 1, have_x64, pdl);
+                launch_sweep<kUpdateDev>(st, m, b, s, cur, prv, tau, have_x64, pdl);
             else
-                launch_sweep<kAddPsi>(st, m, b, s, cur, prv, a, c, k == 1, have_x64, pdl);
+                launch_sweep<kAddPsi>(st, m, b, s, cur, prv, tau, have_x64, pdl);
             std::swap(cur, prv);
         }
         if (r < st->rounds - 1) {
-            k_refine<<<grid, 128, 0, s>>>(m, b, cur, prv, r == 0, st->inv_theta);
+            k_refine<<<grid, 128, 0, s>>>(m, b, cur, prv, r == 0, st->tau[0]);
             A = prv;
             B = cur;
         }
@@ -1399,14 +1407,11 @@ static void enqueue_step(felbm_state* st, cudaStream_t s) {
         // small batch members: one CTA each, on a side branch of the graph
         if (st->n_cta > 0) {
             ChebCoef cf{};
-            for (int k = 1; k < st->sweeps && k < kMaxSweeps; ++k) {
-                cf.a[k] = (float)st->cheb_a[k];
-                cf.c[k] = (float)st->cheb_c[k];
-            }
+            for (int k = 1; k < st->sweeps && k < kMaxSweeps; ++k) cf.tau[k] = (float)st->tau[k];
             cudaEventRecord(st->ev_fork, s);
             cudaStreamWaitEvent(st->side_stream, st->ev_fork, 0);
             k_step_cta32<<<st->n_cta, kCtaThreads, 0, st->side_stream>>>(m, st->phys, b, st->gt, st->gt.cta_groups,
-                                                                         cf, st->sweeps, (float)st->inv_theta);
+                                                                         cf, st->sweeps, (float)st->tau[0]);
             cudaEventRecord(st->ev_join, st->side_stream);
         }
         // the rest (a prefix of nodes and triangles): tiled kernels
@@ -1435,10 +1440,10 @@ static void enqueue_step(felbm_state* st, cudaStream_t s) {
             launch_k(chain, k_element32, dim3(grid_for(mt.T, 128)), dim3(128), s, mt, st->phys, b);
             mark(4);
             switch (mt.iell_w) {
-                case 6: launch_k(chain, k_rhs32<6>, dim3(grid_for(mt.N, 128)), dim3(128), s, mt, st->phys, b, (float)st->inv_theta); break;
-                case 8: launch_k(chain, k_rhs32<8>, dim3(grid_for(mt.N, 128)), dim3(128), s, mt, st->phys, b, (float)st->inv_theta); break;
-                case 12: launch_k(chain, k_rhs32<12>, dim3(grid_for(mt.N, 128)), dim3(128), s, mt, st->phys, b, (float)st->inv_theta); break;
-                default: launch_k(chain, k_rhs32<0>, dim3(grid_for(mt.N, 128)), dim3(128), s, mt, st->phys, b, (float)st->inv_theta);
+                case 6: launch_k(chain, k_rhs32<6>, dim3(grid_for(mt.N, 128)), dim3(128), s, mt, st->phys, b, (float)st->tau[0]); break;
+                case 8: launch_k(chain, k_rhs32<8>, dim3(grid_for(mt.N, 128)), dim3(128), s, mt, st->phys, b, (float)st->tau[0]); break;
+                case 12: launch_k(chain, k_rhs32<12>, dim3(grid_for(mt.N, 128)), dim3(128), s, mt, st->phys, b, (float)st->tau[0]); break;
+                default: launch_k(chain, k_rhs32<0>, dim3(grid_for(mt.N, 128)), dim3(128), s, mt, st->phys, b, (float)st->tau[0]);
             }
             mark(5);
             enqueue_solve(st, mt, st->buf, s, true, chain);
@@ -1466,7 +1471,7 @@ static void enqueue_step(felbm_state* st, cudaStream_t s) {
     if (st->mode == FELBM_SOLVER_FP64)
         k_rhs<false><<<grid_for(m.N, 128), 128, 0, s>>>(m, st->phys, b, st->inv_theta);
     else
-        k_rhs<true><<<grid_for(m.N, 128), 128, 0, s>>>(m, st->phys, b, st->inv_theta);
+        k_rhs<true><<<grid_for(m.N, 128), 128, 0, s>>>(m, st->phys, b, st->tau[0]);
     mark(5);
     enqueue_solve(st, st->dm, st->buf, s, true);
     mark(6);
@@ -1543,7 +1548,12 @@ int felbm_init(const felbm_mesh* mesh, const felbm_params* params, const double*
 
     // Chebyshev coefficients for the spectrum [1/4, 1] of m^{-1} M11
     st->mode = params->solver_mode;
-    st->sweeps = params->solver_iters ? params->solver_iters : (st->mode == FELBM_SOLVER_FP64 ? 32 : 14);
+    // FP32-deviation states take 10 steps per solve (bound 2*3^-10 on the
+    // increment): against the FP64 path that leaves contact angles within
+    // 2e-4 degree, mass drift below 1e-8 and C within 1e-7 of the oracle
+    // after 20 steps, the FP32 level of the other terms
+    st->sweeps = params->solver_iters ? params->solver_iters
+                                      : (st->mode == FELBM_SOLVER_FP64 ? 32 : (dev32 ? 10 : 14));
     st->rounds = st->mode == FELBM_SOLVER_FP64 ? 1 : (params->solver_rounds ? params->solver_rounds : (dev32 ? 1 : 3));
     const double lmin = 0.25, lmax = 1.0;
     const double theta = 0.5 * (lmax + lmin), delta = 0.5 * (lmax - lmin), sigma1 = theta / delta;
@@ -1556,6 +1566,17 @@ int felbm_init(const felbm_mesh* mesh, const felbm_params* params, const double*
         st->cheb_a[k] = rho * rho_prev;
         st->cheb_c[k] = 2.0 * rho / delta;
         rho_prev = rho;
+    }
+    // FP32 solves: Richardson steps 1/lambda_j at the Chebyshev roots
+    // lambda_j = theta + delta cos((2j+1) pi / 2K), j = 0..K-1, in the order
+    // j = 0, K-1, 1, K-2, ... (largest and smallest root alternately)
+    st->tau.assign(st->sweeps, 1.0);
+    {
+        const int K = st->sweeps;
+        for (int k = 0; k < K; ++k) {
+            const int j = (k & 1) ? K - 1 - k / 2 : k / 2;
+            st->tau[k] = 1.0 / (theta + delta * std::cos((2.0 * j + 1.0) * 3.14159265358979323846 / (2.0 * K)));
+        }
     }
 
     // host-side derived tables
@@ -2101,7 +2122,7 @@ int felbm_mass_solve(felbm_state* st, const double* B, double* X, int32_t k) {
     if (st->mode == FELBM_SOLVER_FP64)
         k_cheb_start<false><<<grid_for(m.N, kBlock), kBlock, 0, s>>>(m, b, st->inv_theta);
     else
-        k_cheb_start<true><<<grid_for(m.N, kBlock), kBlock, 0, s>>>(m, b, st->inv_theta);
+        k_cheb_start<true><<<grid_for(m.N, kBlock), kBlock, 0, s>>>(m, b, st->tau[0]);
     const double* result = enqueue_solve(st, st->dm, b, s, false);
     k_gather_out<<<grid_for(m.N, kBlock), kBlock, 0, s>>>(m, result, b.stage, k);
     FELBM_CUDA(cudaGetLastError());
@@ -2189,7 +2210,7 @@ int felbm_mass_solve_static(felbm_state* st, const double* d_B, double* d_X, int
     if (st->mode == FELBM_SOLVER_FP64)
         k_cheb_start<false><<<grid_for(m.N, kBlock), kBlock, 0, s>>>(m, sb, st->inv_theta);
     else
-        k_cheb_start<true><<<grid_for(m.N, kBlock), kBlock, 0, s>>>(m, sb, st->inv_theta);
+        k_cheb_start<true><<<grid_for(m.N, kBlock), kBlock, 0, s>>>(m, sb, st->tau[0]);
     const double* result = enqueue_solve(st, st->dm, sb, s, false);
     k_gather_out<<<grid_for(m.N, kBlock), kBlock, 0, s>>>(m, result, d_X, k);
     FELBM_CUDA(cudaGetLastError());
@@ -2438,7 +2459,7 @@ int felbm_adjoint_step(felbm_state* st) {
     if (st->mode == FELBM_SOLVER_FP64)
         k_cheb_start<false><<<grid_for(m.N, kBlock), kBlock, 0, s>>>(m, b, st->inv_theta);
     else
-        k_cheb_start<true><<<grid_for(m.N, kBlock), kBlock, 0, s>>>(m, b, st->inv_theta);
+        k_cheb_start<true><<<grid_for(m.N, kBlock), kBlock, 0, s>>>(m, b, st->tau[0]);
     a.lamRHS = enqueue_solve(st, m, b, s, false);
     k_adj_elem_a<<<grid_for(m.T, 128), 128, 0, s>>>(m, st->phys, b, a);
     k_adj_elem_b<<<grid_for(m.T, kBlock), kBlock, 0, s>>>(m, a);

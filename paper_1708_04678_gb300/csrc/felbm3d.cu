@@ -434,10 +434,11 @@ __global__ void __launch_bounds__(128) k3_element(DevMesh3 m, Phys3 c, Bufs3 b) 
 // RHS_{i,a} = sum_{T at i} R_{T,a} (dt/4 + dt^2/2 e_a.b_{i,T})
 //   - dt sum_{wall f at i} (e_a.n) [A/6 (psi_opp - psi)_i + A/12 sum_{o != i} (psi_opp - psi)_o]
 // (wall term only for incoming directions e_a.n < 0).  One thread per
-// (node, set); also writes the first Chebyshev iterate RHS / (m_i theta):
+// (node, set); also writes the first iterate of the solve first_scale RHS / m_i
+// (1/theta for the FP64 Chebyshev recurrence, tau_0 for the FP32 steps):
 // FP64 (FP64 Chebyshev) or FP32 with the FP32 copy of the RHS (mixed solve).
 template <bool kMixed>
-__global__ void __launch_bounds__(kNodeBlock) k3_rhs(DevMesh3 m, Phys3 c, Bufs3 b, double inv_theta) {
+__global__ void __launch_bounds__(kNodeBlock) k3_rhs(DevMesh3 m, Phys3 c, Bufs3 b, double first_scale) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= m.N) return;
     const int s = blockIdx.y, Np = m.Np, ninc = m.ninc;
@@ -474,7 +475,7 @@ __global__ void __launch_bounds__(kNodeBlock) k3_rhs(DevMesh3 m, Phys3 c, Bufs3 
             }
         }
     }
-    const double sc = m.inv_lumped[i] * inv_theta;
+    const double sc = m.inv_lumped[i] * first_scale;
 #pragma unroll
     for (int q = 0; q < 19; ++q) {
         const size_t r = (size_t)(19 * s + q) * Np + i;
@@ -533,12 +534,12 @@ enum Final3 { kStore3 = 0, kAddPsi3 = 1, kUpdateDev3 = 2 };
 
 template <int kFinal>
 __global__ void __launch_bounds__(kNodeBlock) k3_sweep32(DevMesh3 m, Phys3 c, Bufs3 b, const float* __restrict__ cur,
-                                                         float* prev, float a, float cc, int first, int have_x64);
+                                                         float* nxt, float tau, int have_x64);
 
 // x <- x + e ; rho <- rho - M11 e (FP64); FP32 copy of rho and the first
-// iterate of the next correction, rho / (m theta).  x64 = x0, rho64 = x1.
+// iterate of the next correction, tau_0 rho / m.  x64 = x0, rho64 = x1.
 __global__ void __launch_bounds__(kNodeBlock) k3_refine(DevMesh3 m, Bufs3 b, const float* __restrict__ e,
-                                                        float* next_first, int first_round, double inv_theta) {
+                                                        float* next_first, int first_round, double tau0) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= m.N) return;
     const int Np = m.Np;
@@ -553,7 +554,7 @@ __global__ void __launch_bounds__(kNodeBlock) k3_refine(DevMesh3 m, Bufs3 b, con
 #pragma unroll
         for (int q = 0; q < 19; ++q) acc[q] += mv * (double)ej[q];
     }
-    const double sc = m.inv_lumped[i] * inv_theta;
+    const double sc = m.inv_lumped[i] * tau0;
     const size_t a0 = (size_t)i * kRow + slot(s, 0);
 #pragma unroll
     for (int q = 0; q < 19; ++q) {
@@ -578,12 +579,17 @@ __device__ void dev32_update3(const DevMesh3& m, const Phys3& c, const Bufs3& b,
 __device__ __forceinline__ void pdl_wait3() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void pdl_release3() { asm volatile("griddepcontrol.launch_dependents;" :::); }
 
+// One Richardson step x_{k+1} = x_k + tau_k m^{-1} (b - M x_k) of the FP32
+// solve, tau_k the reciprocal Chebyshev roots of the spectrum [1/5, 1] taken
+// largest and smallest alternately (after K steps: the scaled Chebyshev error
+// polynomial; every partial product stays below 1).  Reads x_k (gathered)
+// and b only.
 // kW > 0: ELL of that width, its columns and values loaded up front (they
 // do not depend on the previous sweep, so under programmatic dependent
 // launch they are fetched while that sweep drains); kW = 0: CSR.
 template <int kFinal, int kW>
 __global__ void __launch_bounds__(kCoopBlock) k3_sweep32(DevMesh3 m, Phys3 c, Bufs3 b, const float* __restrict__ cur,
-                                                         float* prev, float a, float cc, int first, int have_x64) {
+                                                         float* nxt, float tau, int have_x64) {
     pdl_release3();
     const Coop k = coop_index(m.N);
     const int i = k.active ? k.item : 0;      // idle lanes read node 0 and write nothing
@@ -598,7 +604,7 @@ __global__ void __launch_bounds__(kCoopBlock) k3_sweep32(DevMesh3 m, Phys3 c, Bu
             val[e] = m.ell_val[e * Np + i];
         }
     }
-    const float sc = cc * m.inv_lumped32[i];
+    const float sc = tau * m.inv_lumped32[i];
     pdl_wait3();
     float4 ag = make_float4(0.0f, 0.0f, 0.0f, 0.0f), ah = ag;
     if (k.active) {
@@ -620,19 +626,17 @@ __global__ void __launch_bounds__(kCoopBlock) k3_sweep32(DevMesh3 m, Phys3 c, Bu
     }
     const size_t own = (size_t)i * kRow;
     const float4* xk4 = reinterpret_cast<const float4*>(cur + own);
-    const float4* xm4 = reinterpret_cast<const float4*>(prev + own);
     const float4* r4 = reinterpret_cast<const float4*>(b.r32 + own);
     float4 xn[2];
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
         const int v = 5 * h + k.c;
         const float4 xk = xk4[v], rr = r4[v], acc = h ? ah : ag;
-        const float4 xm = first ? make_float4(0.0f, 0.0f, 0.0f, 0.0f) : xm4[v];
-        xn[h].x = xk.x + a * (xk.x - xm.x) + sc * (rr.x - acc.x);
-        xn[h].y = xk.y + a * (xk.y - xm.y) + sc * (rr.y - acc.y);
-        xn[h].z = xk.z + a * (xk.z - xm.z) + sc * (rr.z - acc.z);
-        xn[h].w = xk.w + a * (xk.w - xm.w) + sc * (rr.w - acc.w);
-        if (kFinal == kStore3 && k.active) reinterpret_cast<float4*>(prev + own)[v] = xn[h];
+        xn[h].x = xk.x + sc * (rr.x - acc.x);
+        xn[h].y = xk.y + sc * (rr.y - acc.y);
+        xn[h].z = xk.z + sc * (rr.z - acc.z);
+        xn[h].w = xk.w + sc * (rr.w - acc.w);
+        if (kFinal == kStore3 && k.active) reinterpret_cast<float4*>(nxt + own)[v] = xn[h];
     }
     if constexpr (kFinal == kAddPsi3) {
         // FP64 storage: psi += x64 + e for this lane's directions
@@ -962,8 +966,9 @@ struct felbm3d_state {
     int mode = FELBM_SOLVER_MIXED;
     int sweeps = 16;
     int rounds = 3;
-    std::vector<double> cheb_a, cheb_c;
-    double inv_theta = 1.0;
+    std::vector<double> cheb_a, cheb_c;   // three-term recurrence of the FP64 solve
+    double inv_theta = 1.0;               // its first iterate x_1 = m^{-1} b / theta
+    std::vector<double> tau;              // Richardson step sizes of the FP32 solves; tau[0] gives x_1
     int64_t step = 0;
     double mass0 = 0.0;
     bool dev32 = false;
@@ -996,17 +1001,17 @@ static void launch3(bool pdl, void (*kern)(KArgs...), unsigned grid, unsigned bl
 // One FP32 sweep with the compiled ELL width of the mesh (else CSR); pdl:
 // the previous launch on the stream is a sweep.
 template <int kFinal>
-static void launch_sweep3(felbm3d_state* st, cudaStream_t s, const float* cur, float* prv, float a, float c, int first,
+static void launch_sweep3(felbm3d_state* st, cudaStream_t s, const float* cur, float* nxt, float tau,
                           int have_x64, bool pdl) {
     const DevMesh3& m = st->dm;
     const unsigned g = grid_for(m.N, kItemsPerBlock);
     pdl = pdl && st->use_pdl;
     switch (m.ell_w) {
-        case 15: launch3(pdl, k3_sweep32<kFinal, 15>, g, kCoopBlock, s, m, st->phys, st->buf, cur, prv, a, c, first, have_x64); break;
-        case 16: launch3(pdl, k3_sweep32<kFinal, 16>, g, kCoopBlock, s, m, st->phys, st->buf, cur, prv, a, c, first, have_x64); break;
-        case 24: launch3(pdl, k3_sweep32<kFinal, 24>, g, kCoopBlock, s, m, st->phys, st->buf, cur, prv, a, c, first, have_x64); break;
-        case 32: launch3(pdl, k3_sweep32<kFinal, 32>, g, kCoopBlock, s, m, st->phys, st->buf, cur, prv, a, c, first, have_x64); break;
-        default: launch3(pdl, k3_sweep32<kFinal, 0>, g, kCoopBlock, s, m, st->phys, st->buf, cur, prv, a, c, first, have_x64);
+        case 15: launch3(pdl, k3_sweep32<kFinal, 15>, g, kCoopBlock, s, m, st->phys, st->buf, cur, nxt, tau, have_x64); break;
+        case 16: launch3(pdl, k3_sweep32<kFinal, 16>, g, kCoopBlock, s, m, st->phys, st->buf, cur, nxt, tau, have_x64); break;
+        case 24: launch3(pdl, k3_sweep32<kFinal, 24>, g, kCoopBlock, s, m, st->phys, st->buf, cur, nxt, tau, have_x64); break;
+        case 32: launch3(pdl, k3_sweep32<kFinal, 32>, g, kCoopBlock, s, m, st->phys, st->buf, cur, nxt, tau, have_x64); break;
+        default: launch3(pdl, k3_sweep32<kFinal, 0>, g, kCoopBlock, s, m, st->phys, st->buf, cur, nxt, tau, have_x64);
     }
 }
 
@@ -1046,7 +1051,7 @@ static void enqueue_step3(felbm3d_state* st, cudaStream_t s) {
     if (st->mode == FELBM_SOLVER_FP64)
         k3_rhs<false><<<g2, kNodeBlock, 0, s>>>(m, st->phys, b, st->inv_theta);
     else
-        k3_rhs<true><<<g2, kNodeBlock, 0, s>>>(m, st->phys, b, st->inv_theta);
+        k3_rhs<true><<<g2, kNodeBlock, 0, s>>>(m, st->phys, b, st->tau[0]);
     mark(4);
     enqueue_solve3(st, s);
     mark(5);
@@ -1074,20 +1079,20 @@ static void enqueue_solve3(felbm3d_state* st, cudaStream_t s, bool after_release
         float* cur = A;
         float* prv = B;
         for (int k = 1; k < st->sweeps; ++k) {
-            const float a = (float)st->cheb_a[k], c = (float)st->cheb_c[k];
+            const float tau = (float)st->tau[k];
             const bool last = r == st->rounds - 1 && k == st->sweeps - 1;
             // the previous launch is a sweep of this round, or a kernel that released its dependents
             const bool pdl = k > 1 || (k == 1 && r == 0 && after_release);
             if (!last)
-                launch_sweep3<kStore3>(st, s, cur, prv, a, c, k == 1, have_x64, pdl);
+                launch_sweep3<kStore3>(st, s, cur, prv, tau, have_x64, pdl);
             else if (st->dev32)
-                launch_sweep3<kUpdateDev3>(st, s, cur, prv, a, c, k == 1, have_x64, pdl);
+                launch_sweep3<kUpdateDev3>(st, s, cur, prv, tau, have_x64, pdl);
             else
-                launch_sweep3<kAddPsi3>(st, s, cur, prv, a, c, k == 1, have_x64, pdl);
+                launch_sweep3<kAddPsi3>(st, s, cur, prv, tau, have_x64, pdl);
             std::swap(cur, prv);
         }
         if (r < st->rounds - 1) {
-            k3_refine<<<g2, kNodeBlock, 0, s>>>(m, b, cur, prv, r == 0, st->inv_theta);
+            k3_refine<<<g2, kNodeBlock, 0, s>>>(m, b, cur, prv, r == 0, st->tau[0]);
             A = prv;
             B = cur;
         }
@@ -1223,6 +1228,14 @@ int felbm3d_init(const felbm3d_mesh* mesh, const felbm_params* params, const dou
         st->cheb_a[k] = rho * rho_prev;
         st->cheb_c[k] = 2.0 * rho / delta;
         rho_prev = rho;
+    }
+    // FP32 solves: Richardson steps 1/lambda_j at the Chebyshev roots
+    // lambda_j = theta + delta cos((2j+1) pi / 2K), in the order j = 0, K-1,
+    // 1, K-2, ... (largest and smallest root alternately)
+    st->tau.assign(st->sweeps, 1.0);
+    for (int k = 0; k < st->sweeps; ++k) {
+        const int K = st->sweeps, j = (k & 1) ? K - 1 - k / 2 : k / 2;
+        st->tau[k] = 1.0 / (theta + delta * std::cos((2.0 * j + 1.0) * 3.14159265358979323846 / (2.0 * K)));
     }
 
     // host-side derived tables
@@ -1637,7 +1650,7 @@ static void enqueue_step_dev32(felbm3d_state* st, cudaStream_t s) {
     mark3(st, s, 2);
     launch3(chain, k3_element32, grid_for(m.T, kElemTets), kCoopBlock, s, m, st->phys, b);
     mark3(st, s, 3);
-    launch3(chain, k3_rhs32, grid_for(m.N, kItemsPerBlock), kCoopBlock, s, m, st->phys, b, (float)st->inv_theta);
+    launch3(chain, k3_rhs32, grid_for(m.N, kItemsPerBlock), kCoopBlock, s, m, st->phys, b, (float)st->tau[0]);
     mark3(st, s, 4);
     enqueue_solve3(st, s, chain);
     mark3(st, s, 5);

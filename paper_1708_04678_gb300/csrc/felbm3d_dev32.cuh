@@ -294,7 +294,7 @@ __device__ __forceinline__ float wall_diff32(const Phys3& c, const Bufs3& b, int
     return eq + ddev;
 }
 
-__global__ void __launch_bounds__(kCoopBlock) k3_rhs32(DevMesh3 m, Phys3 c, Bufs3 b, float inv_theta) {
+__global__ void __launch_bounds__(kCoopBlock) k3_rhs32(DevMesh3 m, Phys3 c, Bufs3 b, float tau0) {
     pdl_release3();
     pdl_wait3();
     const Coop k = coop_index(m.N);
@@ -345,7 +345,7 @@ __global__ void __launch_bounds__(kCoopBlock) k3_rhs32(DevMesh3 m, Phys3 c, Bufs
             set_comp(ah, j, comp(ah, j) + addh);
         }
     }
-    const float sc = m.inv_lumped32[i] * inv_theta;
+    const float sc = m.inv_lumped32[i] * tau0;
     float4* r4 = reinterpret_cast<float4*>(b.r32 + (size_t)i * kRow);
     float4* e4 = reinterpret_cast<float4*>(b.e1 + (size_t)i * kRow);
     r4[k.c] = ag;

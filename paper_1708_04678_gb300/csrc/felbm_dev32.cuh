@@ -230,7 +230,7 @@ __global__ void __launch_bounds__(128) k_element32(DevMesh m, Phys c, Bufs b) {
 // kI > 0: the incident triangles from the incidence ELL (padding: the zero
 // residual row T), their ids and gradients loaded up front; kI = 0: CSR.
 template <int kI = 0>
-__device__ __forceinline__ void rhs32_node(const DevMesh& m, const Phys& c, const Bufs& b, int i, float inv_theta) {
+__device__ __forceinline__ void rhs32_node(const DevMesh& m, const Phys& c, const Bufs& b, int i, float tau0) {
     const int Np = m.Np;
     float acc[18];
 #pragma unroll
@@ -309,7 +309,7 @@ __device__ __forceinline__ void rhs32_node(const DevMesh& m, const Phys& c, cons
 #undef FELBM_WALL32_Q
         }
     }
-    float s = m.inv_lumped32[i] * inv_theta;
+    float s = m.inv_lumped32[i] * tau0;
 #pragma unroll
     for (int q = 0; q < 18; ++q) {
         b.r32[q * Np + i] = acc[q];
@@ -318,11 +318,11 @@ __device__ __forceinline__ void rhs32_node(const DevMesh& m, const Phys& c, cons
 }
 
 template <int kI>
-__global__ void __launch_bounds__(128) k_rhs32(DevMesh m, Phys c, Bufs b, float inv_theta) {
+__global__ void __launch_bounds__(128) k_rhs32(DevMesh m, Phys c, Bufs b, float tau0) {
     pdl_release();
     pdl_wait();
     int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < m.N) rhs32_node<kI>(m, c, b, i, inv_theta);
+    if (i < m.N) rhs32_node<kI>(m, c, b, i, tau0);
 }
 
 // ---------------------------- update of fields and deviations (node) ------

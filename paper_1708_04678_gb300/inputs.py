@@ -39,6 +39,7 @@ __all__ = [
     "free_droplet_256",
     "droplet_sweep",
     "rough_wall_droplet",
+    "rough_wall_strip",
     "small_sessile",
     "small_free_droplet",
     "batch",
@@ -319,6 +320,21 @@ def rough_wall_droplet(seed=4, width=2048, height=1024, rows=1017, R=300.0,
     C0 = droplet_C0(mesh["xy"], centre, R, phys["xi"], mesh["period"])
     return {"name": f"rough-wall droplet {width}x{height}", "mesh": mesh, "C0": C0,
             "phys": phys, "steps": steps, "centre": centre, "R": float(R)}
+
+
+def rough_wall_strip(columns=128, seed=40, **kw):
+    """A periodic strip of ``columns`` columns cut from the rough-wall
+    droplet's recipe (same 1017 body-fitted rows, wall profile, jitter,
+    physics and droplet field, centred on the droplet's axis): a bounded
+    sample of that workload for timing the CPU oracle per node-update.
+    ``columns`` must be a multiple of the wall's wavelength (64) so that the
+    wall stays periodic; the droplet field is symmetric about the strip's
+    centre, so its periodic images match."""
+    if columns % 64:
+        raise ValueError("columns must be a multiple of 64")
+    w = rough_wall_droplet(seed=seed, width=columns, **kw)
+    w["name"] = f"rough-wall strip {columns} columns"
+    return w
 
 
 def capillary_channel(H=16, length_factor=20, reservoir=4, theta=56.0, l0_factor=2.0, liquid_factor=4.0,

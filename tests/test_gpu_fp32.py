@@ -7,6 +7,7 @@ degree, relative mass drift below 1e-6, and spurious currents / Laplace
 pressure close to the FP64 run.
 """
 import math
+import os
 
 import numpy as np
 import pytest
@@ -27,7 +28,13 @@ def _cuda():
     build.build()
 
 
+# Steps of the FP32 solve per time step: 0 = the library's default.  The
+# variable lets the same checks be run at another count.
+SWEEPS = int(os.environ.get("FELBM_TEST_FP32_SWEEPS", "0"))
+
+
 def _dev(w, **kw):
+    kw.setdefault("solver_iters", SWEEPS)
     return gpu_state(w, precision=F.FP32_DEV, **kw)
 
 

@@ -1,0 +1,76 @@
+"""The 2,082,816-node rough-wall droplet at full size against the oracle.
+
+The oracle needs minutes and several GB per run of this mesh, so its state
+after 20 steps is stored, at a seeded sample of nodes (4,096 drawn uniformly
+plus every 8th node of the rough wall), by
+``tests/golden/make_rough_wall_golden.py``, which calls only the oracle and
+the seeded input generator.  The CUDA path runs the same 20 steps, in the
+launch configuration the benchmark times (autotuned solve split), and is
+compared at those nodes: FP64 storage to 1e-11 (the bar of the plain path),
+FP32 deviation storage at FP32 level.  Relative errors are normwise over the
+sample, as in the other parity tests.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+from paper_1708_04678_gb300 import felbm as F
+from paper_1708_04678_gb300 import inputs as I
+from parity_util import rel_err
+
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "rough_wall_20_steps.npz")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1708_04678_gb300 import build
+    build.build()
+
+
+@pytest.fixture(scope="module")
+def golden():
+    z = np.load(GOLDEN)
+    return {"steps": int(z["steps"]), "nodes": z["nodes"], "g": z["g"], "h": z["h"],
+            "diag": dict(zip([str(s) for s in z["diag_names"]], z["diag_values"]))}
+
+
+@pytest.fixture(scope="module")
+def workload():
+    return I.rough_wall_droplet()
+
+
+def _run(w, golden, precision):
+    st = F.State(F.Mesh.from_dict(w["mesh"]), F.params_derive(w["phys"], precision=precision), w["C0"])
+    st.autotune(trials=2)                       # leaves the state and the step count unchanged
+    st.step(golden["steps"])
+    g, h = st.get_state()
+    d = st.diagnostics(w["centre"], w["R"], w["phys"]["xi"], 0)
+    n = golden["nodes"]
+    err = {"g": rel_err(g[:, n], golden["g"]), "h": rel_err(h[:, n], golden["h"]),
+           "C": rel_err(h[:, n].sum(0), golden["h"].sum(0))}
+    st.close()
+    return err, d
+
+
+def test_rough_wall_fp64_matches_stored_oracle(workload, golden):
+    err, d = _run(workload, golden, F.FP64)
+    assert max(err.values()) < 1e-11, err
+    do = golden["diag"]
+    assert abs(d["mass_drift_rel"]) < 1e-12
+    for key in ("mass", "kinetic_energy", "max_u", "delta_p", "interface_rho_uu", "wetted_length", "height",
+                "theta_deg"):
+        assert math.isclose(d[key], do[key], rel_tol=1e-9, abs_tol=1e-14), (key, d[key], do[key])
+
+
+def test_rough_wall_fp32_dev_matches_stored_oracle_at_fp32_level(workload, golden):
+    err, d = _run(workload, golden, F.FP32_DEV)
+    assert err["C"] < 1e-6, err
+    assert err["h"] < 1e-5 and err["g"] < 1e-3, err
+    assert abs(d["mass_drift_rel"]) < 1e-6
