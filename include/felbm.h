@@ -14,7 +14,9 @@
  *    throws across the ABI.
  *  - Host arrays are owned by the caller and only read (or written) during
  *    the call.  Node numbering is the caller's: the library reorders nodes
- *    internally (reverse Cuthill-McKee) and converts back on every exchange.
+ *    internally (compact tiles of at most 1024 nodes by recursive coordinate
+ *    bisection, reverse Cuthill-McKee order inside a tile) and converts back
+ *    on every exchange.
  *  - Device memory: the library never allocates it.  The caller allocates one
  *    workspace of felbm_workspace_bytes() bytes (any allocator, 256-byte
  *    aligned) and keeps it alive until felbm_state_destroy().
@@ -22,7 +24,8 @@
  *    to felbm_init (passed as void*; NULL = legacy default stream).  Calls
  *    that return host data synchronise that stream; felbm_step does not.
  *  - Environment: FELBM_PDL=0 launches the solve sweeps without programmatic
- *    dependent launch (read at felbm_init; default on).
+ *    dependent launch (read at felbm_init; default on).  FELBM_ORDER=rcm
+ *    (read at mesh creation) keeps the plain reverse Cuthill-McKee order.
  *  - Distribution layout on the host: double [9][n_nodes], direction-major,
  *    D2Q9 order e_0 = (0,0), e_1..e_4 = (1,0),(0,1),(-1,0),(0,-1),
  *    e_5..e_8 = (1,1),(-1,1),(-1,-1),(1,-1); weights 4/9, 1/9, 1/36.
@@ -123,8 +126,10 @@ typedef struct felbm_mesh_info {
     int32_t n_groups;         /* connected components (independent droplets of a batch) */
     int32_t nnz;              /* entries of the node-node sparsity pattern */
     int32_t max_degree;       /* largest row of that pattern */
-    int32_t bandwidth;        /* after reverse Cuthill-McKee */
+    int32_t bandwidth;        /* largest |i - j| of the pattern in the internal order */
     double min_area, total_area;
+    int32_t n_tiles;          /* node tiles of the internal order (at most 1024 nodes each) */
+    int32_t max_tile_halo;    /* most nodes outside a tile that its rows reference */
 } felbm_mesh_info;
 
 /* What felbm_diagnostics measures beside the global sums. */
@@ -266,9 +271,26 @@ int felbm_batch_schedule(felbm_state* state, int32_t cta_max_nodes);
  * other value. */
 int felbm_sweep_parts(felbm_state* state, int32_t parts);
 
+/* Where the FP32 store sweeps of the solve read the iterate x_k (states with
+ * an FP32 solve and an ELL pattern).  0: each thread gathers its row's
+ * neighbours from global memory.  1: one thread block per (node tile, part
+ * of the right-hand sides) copies the tile's run of each iterate row into
+ * shared memory with 1D TMA bulk copies, gathers the tile's halo beside it,
+ * and forms the row products from shared memory.  Same arithmetic in the
+ * same order: the trajectory does not depend on it.  FELBM_ERR_UNSUPPORTED
+ * if a tile's halo exceeds the staged rows (504 nodes).  A tiled sweep whose
+ * copy has not landed after 0.2 s stops (and later blocks skip their work)
+ * and sets an error bit that the next felbm_diagnostics or felbm_get_state
+ * reports as FELBM_ERR_CUDA.
+ * The step graph is rebuilt at the next felbm_step.  Default 0;
+ * felbm_autotune picks one by timing. */
+int felbm_sweep_tiled(felbm_state* state, int32_t on);
+
 typedef struct felbm_tune_result {
     int32_t sweep_parts;     /* chosen threads per node of the FP32 solve sweeps */
     float parts_ms[4];       /* step time with 1, 2, 3, 6 threads per node (0 = not timed) */
+    int32_t sweep_tiled;     /* 1: the tiled store sweeps were chosen (felbm_sweep_tiled) */
+    float tiled_ms[4];       /* step time of the tiled sweeps with 1, 2, 3, 6 parts (0 = not timed) */
     int32_t cta_max_nodes;   /* chosen batch threshold (0 = tiled only) */
     int32_t n_candidates;
     int32_t candidates[16];  /* thresholds timed */
@@ -278,7 +300,7 @@ typedef struct felbm_tune_result {
 /* Autotuner: times `trials` steps (after one warm-up step) per candidate and
  * keeps the fastest -- first the threads per node of the FP32 solve sweeps
  * (1, 2, 3 or 6; states with an FP32 solve and an ELL pattern; see
- * felbm_sweep_parts), then, for
+ * felbm_sweep_parts), each gathered and tiled (felbm_sweep_tiled), then, for
  * FP32_DEV batches, each distinct split of the members (tiled only, CTA per
  * member up to 2^11 .. 2^17 nodes).  The state and the step count are saved
  * before and restored after, so the simulation is unchanged.  Synchronises. */

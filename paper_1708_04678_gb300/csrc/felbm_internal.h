@@ -16,8 +16,12 @@ void set_error(const std::string& msg);
 std::vector<int32_t> rcm_order(int32_t N, const std::vector<int32_t>& adj_ptr,
                                const std::vector<int32_t>& adj);
 
-// Host mesh after preprocessing.  Node ids are the internal (reverse
-// Cuthill-McKee) ids; perm[new] = caller id, iperm[caller] = new.
+// Most nodes in one tile of the tiled solve step (see HostMesh::tile_ptr).
+constexpr int32_t kTileNodes = 1024;
+
+// Host mesh after preprocessing.  Node ids are the internal ids (node tiles
+// of recursive coordinate bisection, reverse Cuthill-McKee order inside a
+// tile); perm[new] = caller id, iperm[caller] = new.
 struct HostMesh {
     int32_t N = 0, T = 0, E = 0;
     double period[2] = {0.0, 0.0};
@@ -45,6 +49,12 @@ struct HostMesh {
     std::vector<int32_t> winc_ptr, winc_edge;
     double min_area = 0.0, total_area = 0.0;
     int32_t max_degree = 0, bandwidth = 0;
+    // node tiles: tile k holds the internal nodes [tile_ptr[k], tile_ptr[k+1]),
+    // at most kTileNodes, all in one component; its halo is the sorted list
+    // of nodes outside it that share a matrix row entry with one inside
+    std::vector<int32_t> tile_ptr;
+    std::vector<int32_t> halo_ptr, halo;
+    int32_t max_halo = 0;
     // connected components ("groups"), numbered by their lowest caller node
     // id; each occupies a contiguous range of internal nodes and triangles
     int32_t G = 0;

@@ -9,6 +9,7 @@
 #include <cmath>
 #include <cstdio>
 #include <climits>
+#include <cstdlib>
 #include <cstring>
 #include <deque>
 #include <numeric>
@@ -99,6 +100,34 @@ std::vector<int32_t> rcm_order(int32_t N, const std::vector<int32_t>& adj_ptr,
     }
     std::reverse(order.begin(), order.end());
     return order;
+}
+
+// Cut the nodes nodes[lo, hi) into tiles of at most kTileNodes by recursive
+// coordinate bisection: split at the median of the longer side of their
+// bounding box, recurse into both halves in turn (so consecutive tiles are
+// neighbours in space), and record the end of every tile in `ends`.
+static void bisect_tiles(std::vector<int32_t>& nodes, int64_t lo, int64_t hi, const double* xy,
+                         std::vector<int64_t>& ends) {
+    if (hi - lo <= kTileNodes) {
+        ends.push_back(hi);
+        return;
+    }
+    double x0 = 1e300, x1 = -1e300, y0 = 1e300, y1 = -1e300;
+    for (int64_t k = lo; k < hi; ++k) {
+        const double x = xy[2 * (size_t)nodes[k]], y = xy[2 * (size_t)nodes[k] + 1];
+        x0 = std::min(x0, x);
+        x1 = std::max(x1, x);
+        y0 = std::min(y0, y);
+        y1 = std::max(y1, y);
+    }
+    const int axis = (x1 - x0) >= (y1 - y0) ? 0 : 1;
+    const int64_t mid = lo + (hi - lo) / 2;
+    std::nth_element(nodes.begin() + lo, nodes.begin() + mid, nodes.begin() + hi, [&](int32_t a, int32_t b) {
+        const double ca = xy[2 * (size_t)a + axis], cb = xy[2 * (size_t)b + axis];
+        return ca < cb || (ca == cb && a < b);
+    });
+    bisect_tiles(nodes, lo, mid, xy, ends);
+    bisect_tiles(nodes, mid, hi, xy, ends);
 }
 
 // node_px / node_py: periodic lengths of the sub-mesh each node belongs to
@@ -278,6 +307,35 @@ static int build_mesh(const double* xy, int32_t N, const int32_t* tri_in, int32_
             std::stable_sort(m.perm.begin(), m.perm.end(), [&](int32_t a, int32_t b) {
                 return csize[comp_of[a]] > csize[comp_of[b]];
             });
+        // Node tiles within each component's run.  Recursive coordinate
+        // bisection makes compact tiles, the nodes of a tile keep their
+        // reverse Cuthill-McKee order; FELBM_ORDER=rcm keeps the plain
+        // reverse Cuthill-McKee order and cuts it into runs of kTileNodes.
+        const char* env = std::getenv("FELBM_ORDER");
+        const bool plain_rcm = env && std::string(env) == "rcm";
+        std::vector<int32_t> rank(N);
+        for (int32_t n = 0; n < N; ++n) rank[m.perm[n]] = n;
+        m.tile_ptr.assign(1, 0);
+        std::vector<int64_t> ends;
+        for (int64_t a = 0; a < N;) {
+            int64_t b = a;
+            while (b < N && comp_of[m.perm[b]] == comp_of[m.perm[a]]) ++b;
+            ends.clear();
+            if (plain_rcm) {
+                for (int64_t e = a + kTileNodes; e < b; e += kTileNodes) ends.push_back(e);
+                ends.push_back(b);
+            } else {
+                bisect_tiles(m.perm, a, b, xy, ends);
+                int64_t s0 = a;
+                for (int64_t e : ends) {
+                    std::sort(m.perm.begin() + s0, m.perm.begin() + e,
+                              [&](int32_t u, int32_t v) { return rank[u] < rank[v]; });
+                    s0 = e;
+                }
+            }
+            for (int64_t e : ends) m.tile_ptr.push_back((int32_t)e);
+            a = b;
+        }
     }
     m.iperm.assign(N, 0);
     for (int32_t n = 0; n < N; ++n) m.iperm[m.perm[n]] = n;
@@ -386,6 +444,27 @@ static int build_mesh(const double* xy, int32_t N, const int32_t* tri_in, int32_
             m.stiff.insert(m.stiff.end(), rk.begin(), rk.end());
             m.row_ptr[i + 1] = (int32_t)m.col.size();
             m.max_degree = std::max(m.max_degree, (int32_t)row.size());
+        }
+    }
+
+    // ---- halo of every node tile ---------------------------------------
+    {
+        const int32_t ntile = (int32_t)m.tile_ptr.size() - 1;
+        m.halo_ptr.assign(ntile + 1, 0);
+        m.halo.clear();
+        m.max_halo = 0;
+        std::vector<int32_t> h;
+        for (int32_t k = 0; k < ntile; ++k) {
+            const int32_t s0 = m.tile_ptr[k], s1 = m.tile_ptr[k + 1];
+            h.clear();
+            for (int32_t i = s0; i < s1; ++i)
+                for (int32_t p = m.row_ptr[i]; p < m.row_ptr[i + 1]; ++p)
+                    if (m.col[p] < s0 || m.col[p] >= s1) h.push_back(m.col[p]);
+            std::sort(h.begin(), h.end());
+            h.erase(std::unique(h.begin(), h.end()), h.end());
+            m.halo.insert(m.halo.end(), h.begin(), h.end());
+            m.halo_ptr[k + 1] = (int32_t)m.halo.size();
+            m.max_halo = std::max(m.max_halo, (int32_t)h.size());
         }
     }
 
@@ -644,6 +723,8 @@ int felbm_mesh_info_get(const felbm_mesh* mesh, felbm_mesh_info* out) {
     out->bandwidth = m.bandwidth;
     out->min_area = m.min_area;
     out->total_area = m.total_area;
+    out->n_tiles = m.tile_ptr.empty() ? 0 : (int32_t)m.tile_ptr.size() - 1;
+    out->max_tile_halo = m.max_halo;
     return FELBM_OK;
 }
 

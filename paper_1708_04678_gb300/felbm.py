@@ -49,7 +49,8 @@ class MeshInfo(ctypes.Structure):
     _fields_ = [("n_nodes", ctypes.c_int32), ("n_tri", ctypes.c_int32),
                 ("n_wall_edges", ctypes.c_int32), ("n_groups", ctypes.c_int32), ("nnz", ctypes.c_int32),
                 ("max_degree", ctypes.c_int32), ("bandwidth", ctypes.c_int32),
-                ("min_area", ctypes.c_double), ("total_area", ctypes.c_double)]
+                ("min_area", ctypes.c_double), ("total_area", ctypes.c_double),
+                ("n_tiles", ctypes.c_int32), ("max_tile_halo", ctypes.c_int32)]
 
 
 class MeshDesc(ctypes.Structure):
@@ -88,13 +89,15 @@ class StepTiming(ctypes.Structure):
 
 class TuneResult(ctypes.Structure):
     _fields_ = [("sweep_parts", ctypes.c_int32), ("parts_ms", ctypes.c_float * 4),
+                ("sweep_tiled", ctypes.c_int32), ("tiled_ms", ctypes.c_float * 4),
                 ("cta_max_nodes", ctypes.c_int32), ("n_candidates", ctypes.c_int32),
                 ("candidates", ctypes.c_int32 * 16), ("step_ms", ctypes.c_float * 16)]
 
     def as_dict(self):
         n = self.n_candidates
-        return {"sweep_parts": self.sweep_parts,
+        return {"sweep_parts": self.sweep_parts, "sweep_tiled": self.sweep_tiled,
                 "parts_ms": dict(zip((1, 2, 3, 6), [round(x, 5) for x in self.parts_ms])),
+                "tiled_ms": dict(zip((1, 2, 3, 6), [round(x, 5) for x in self.tiled_ms])),
                 "cta_max_nodes": self.cta_max_nodes,
                 "candidates": list(self.candidates[:n]), "step_ms": list(self.step_ms[:n])}
 
@@ -136,6 +139,7 @@ def _declare(lib):
         "felbm_checkpoint_load": (ctypes.c_int, [_P, _P]),
         "felbm_batch_schedule": (ctypes.c_int, [_P, _I32]),
         "felbm_sweep_parts": (ctypes.c_int, [_P, _I32]),
+        "felbm_sweep_tiled": (ctypes.c_int, [_P, _I32]),
         "felbm_diagnostics_enqueue": (ctypes.c_int, [_P, ctypes.POINTER(DiagRequest), _P]),
         "felbm_diag_finish": (ctypes.c_int, [_P, ctypes.POINTER(DiagRequest), _P, ctypes.POINTER(Diag)]),
         "felbm_autotune": (ctypes.c_int, [_P, _I32, ctypes.POINTER(TuneResult)]),
@@ -467,6 +471,9 @@ class State:
 
     def sweep_parts(self, parts):
         _check(lib().felbm_sweep_parts(self.handle, int(parts)))
+
+    def sweep_tiled(self, on=True):
+        _check(lib().felbm_sweep_tiled(self.handle, 1 if on else 0))
 
     def autotune(self, trials=5):
         r = TuneResult()

@@ -60,7 +60,10 @@ def test_mesh_tables(lib):
     assert info["max_degree"] == 7                       # 6 neighbours + itself on the '/' grid
     assert info["nnz"] == 7 * 64 * 33 - 2 * 64 * 2      # wall rows have 5 entries
     assert abs(info["total_area"] - 64 * 32) < 1e-9
-    assert info["bandwidth"] < 3 * 64                   # reverse Cuthill-McKee keeps rows near the diagonal
+    # node tiles: at most 1024 nodes each, compact (bisection), so a tile's
+    # halo is a thin ring: 2,112 nodes -> 4 tiles of ~528
+    assert info["n_tiles"] == 4
+    assert 0 < info["max_tile_halo"] < 4 * 32
     p = F.params_derive(w["phys"])
     assert mesh.workspace_bytes(p) > 18 * 8 * info["n_nodes"]
 
@@ -175,6 +178,20 @@ def test_channel_mesh_with_a_hole(lib):
     assert info["n_wall_edges"] == 2 * L + 2 * (2 * H)
     assert abs(info["total_area"] - (nx * ny - L * 2 * H)) < 1e-9
     assert info["n_groups"] == 1
+
+
+def test_node_tiles_of_the_workloads():
+    """Tiles cover every node with at most 1024 nodes and a halo that fits the
+    staged rows of the tiled solve step (504), on the rough-wall droplet, the
+    free droplet and a batch of droplets (tiles never span members)."""
+    for w, n_tiles in ((I.rough_wall_droplet(width=256, height=128, rows=129, R=40.0), 64),
+                       (I.free_droplet_256(n=64), 8)):
+        info = F.Mesh.from_dict(w["mesh"]).info()
+        assert info["n_tiles"] == n_tiles, info
+        assert info["max_tile_halo"] < 200, info
+    b = I.batch(I.droplet_sweep(count=4, w_min=64, w_max=96))
+    info = F.Mesh.batch(b["meshes"]).info()
+    assert info["n_tiles"] >= 4 * 2 and info["max_tile_halo"] < 200, info
 
 
 def test_static_solve_arguments_are_validated_before_any_launch():
