@@ -271,14 +271,19 @@ int felbm_batch_schedule(felbm_state* state, int32_t cta_max_nodes);
  * other value. */
 int felbm_sweep_parts(felbm_state* state, int32_t parts);
 
-/* Where the FP32 store sweeps of the solve read the iterate x_k (states with
+/* Where the FP32 store sweeps of the solve read their operands (states with
  * an FP32 solve and an ELL pattern).  0: each thread gathers its row's
- * neighbours from global memory.  1: one thread block per (node tile, part
- * of the right-hand sides) copies the tile's run of each iterate row into
- * shared memory with 1D TMA bulk copies, gathers the tile's halo beside it,
- * and forms the row products from shared memory.  Same arithmetic in the
- * same order: the trajectory does not depend on it.  FELBM_ERR_UNSUPPORTED
- * if a tile's halo exceeds the staged rows (504 nodes).  A tiled sweep whose
+ * neighbours from global memory.  1: a persistent grid, one block per SM,
+ * walks (node tile, part of the right-hand sides) items through up to four
+ * stages of shared memory: 1D TMA bulk copies bring the tile's runs of the iterate,
+ * right-hand side, ELL rows and inverse lumped mass, cp.async the tile's
+ * halo, while the block computes an earlier item from another stage.
+ * The tiled step splits the 18 right-hand sides in 3 or 6 parts (the
+ * felbm_sweep_parts value if it is one of those and fits, else 6).  Same
+ * arithmetic in the same order: the trajectory does not depend on it.
+ * FELBM_ERR_UNSUPPORTED if a tile's halo exceeds the staged rows (504
+ * nodes) or the rows are too long for two stages.  On the meshes measured
+ * here the gathered form is faster (the autotuner keeps it).  A tiled sweep whose
  * copy has not landed after 0.2 s stops (and later blocks skip their work)
  * and sets an error bit that the next felbm_diagnostics or felbm_get_state
  * reports as FELBM_ERR_CUDA.

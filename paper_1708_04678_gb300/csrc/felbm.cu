@@ -1088,6 +1088,8 @@ struct felbm_state {
     bool use_pdl = true;  // programmatic dependent launch between solve sweeps
     int sweep_parts = 2;  // threads per node of the FP32 store sweeps (1, 2, 3, 6)
     bool sweep_tiled = false;  // store sweeps stage each node tile in shared memory (k_sweep_tile32)
+    int n_sm = 1;              // multiprocessors of the device (grid of the persistent tiled step)
+    int smem_optin = 0;        // largest dynamic shared memory a block may opt into
     felbm::GroupTables gt{};
     felbm::AdjBufs adj{};         // adjoint buffers (FP64 states)
     std::vector<double> gmass0;   // per-group mass at felbm_init
@@ -1313,47 +1315,59 @@ static void launch_k(bool pdl, void (*kern)(KArgs...), dim3 grid, dim3 block, cu
 // One FP32 Chebyshev sweep: the ELL kernel of the mesh's width, else CSR.
 // pdl: the previous launch on the stream is a sweep (a kernel that waits).
 // parts: threads per node for the store sweeps (1, 2, 3 or 6; autotuned).
-// The tiled store step (k_sweep_tile32): one block per (tile, part).
+// The tiled store step (k_sweep_tile32): a persistent grid of one block per
+// SM walking the (tile, part) items through its pipeline stages.
 template <int kW, int kParts>
-static void launch_tile_w(const DevMesh& m, const Bufs& b, cudaStream_t s, const float* cur, float* nxt, float tau,
-                          bool pdl) {
+static void launch_tile_w(const felbm_state* st, const DevMesh& m, const Bufs& b, cudaStream_t s, const float* cur,
+                          float* nxt, float tau, bool pdl) {
     cudaLaunchConfig_t cfg{};
-    cfg.gridDim = dim3((unsigned)m.n_tiles * kParts);
+    const int items = m.n_tiles * kParts;
+    cfg.gridDim = dim3((unsigned)std::min(items, st->n_sm));
     cfg.blockDim = dim3(kTileThreads);
-    cfg.dynamicSmemBytes = (size_t)(18 / kParts) * kTileRow * sizeof(float);
+    cfg.dynamicSmemBytes = tile_stages(18 / kParts, kW) * tile_stage_bytes(18 / kParts, kW);
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = pdl ? 1 : 0;
-    cudaLaunchKernelEx(&cfg, k_sweep_tile32<kW, kParts>, m, b, cur, nxt, tau);
+    if constexpr (tile_stages(18 / kParts, kW) >= 2) cudaLaunchKernelEx(&cfg, k_sweep_tile32<kW, kParts>, m, b, cur, nxt, tau);
+}
+
+// Parts of the 18 right-hand sides per work item of the tiled step: 3 if
+// requested (1, 2 or 3) and two or more stages fit the shared memory of a
+// block, else 6; 0 if not even that fits.
+static bool tile_fits(int parts, int ell_w, int smem_optin) {
+    const int nq = 18 / parts;
+    return tile_stages(nq, ell_w) >= 2 &&
+           tile_stages(nq, ell_w) * tile_stage_bytes(nq, ell_w) + 1024 <= (size_t)smem_optin;
+}
+static int tile_parts(const felbm_state* st, int ell_w) {
+    for (int p : {3, 6})
+        if (p >= st->sweep_parts && tile_fits(p, ell_w, st->smem_optin)) return p;
+    return 0;
 }
 
 template <int kW>
 static void launch_tile(const felbm_state* st, const DevMesh& m, const Bufs& b, cudaStream_t s, const float* cur,
                         float* nxt, float tau, bool pdl) {
-    switch (st->sweep_parts) {
-        case 1: launch_tile_w<kW, 1>(m, b, s, cur, nxt, tau, pdl); break;
-        case 3: launch_tile_w<kW, 3>(m, b, s, cur, nxt, tau, pdl); break;
-        case 6: launch_tile_w<kW, 6>(m, b, s, cur, nxt, tau, pdl); break;
-        default: launch_tile_w<kW, 2>(m, b, s, cur, nxt, tau, pdl);
-    }
+    if (tile_parts(st, kW) == 3)
+        launch_tile_w<kW, 3>(st, m, b, s, cur, nxt, tau, pdl);
+    else
+        launch_tile_w<kW, 6>(st, m, b, s, cur, nxt, tau, pdl);
 }
 
-// Shared memory beyond the default 48 KB for the tiled steps (once per process).
+// Shared memory beyond the default 48 KB for the tiled steps that fit.
 template <int kW>
-static cudaError_t allow_tile_smem() {
+static cudaError_t allow_tile_smem(int smem_optin) {
     cudaError_t e = cudaSuccess;
     auto set = [&](auto kern, int parts) {
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)((18 / parts) * kTileRow * sizeof(float)));
+        const size_t bytes = tile_stages(18 / parts, kW) * tile_stage_bytes(18 / parts, kW);
+        if (e == cudaSuccess && tile_fits(parts, kW, smem_optin))
+            e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     };
-    set(k_sweep_tile32<kW, 1>, 1);
-    set(k_sweep_tile32<kW, 2>, 2);
-    set(k_sweep_tile32<kW, 3>, 3);
-    set(k_sweep_tile32<kW, 6>, 6);
+    if constexpr (tile_stages(6, kW) >= 2) set(k_sweep_tile32<kW, 3>, 3);
+    if constexpr (tile_stages(3, kW) >= 2) set(k_sweep_tile32<kW, 6>, 6);
     return e;
 }
 
@@ -1362,7 +1376,7 @@ static void launch_sweep_w(felbm_state* st, const DevMesh& m, const Bufs& b, cud
                            float* nxt, float tau, int have_x64, bool pdl) {
     if constexpr (kFinal == kStore) {
         // the tiled form covers whole meshes (not the tiled prefix of a hybrid batch schedule)
-        if (st->sweep_tiled && m.tiled_ok && m.N == st->dm.N) {
+        if (st->sweep_tiled && m.tiled_ok && m.N == st->dm.N && tile_parts(st, kW) > 0) {
             launch_tile<kW>(st, m, b, s, cur, nxt, tau, pdl);
             return;
         }
@@ -1758,12 +1772,17 @@ int felbm_init(const felbm_mesh* mesh, const felbm_params* params, const double*
     UP(d.halo_ptr, h.halo_ptr);
     UP(d.halo, h.halo);
     if (e == cudaSuccess) e = cudaMemsetAsync(st->buf.kerr, 0, sizeof(unsigned), s);
+    int cur_dev = 0;
+    if (e == cudaSuccess) e = cudaGetDevice(&cur_dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&st->n_sm, cudaDevAttrMultiProcessorCount, cur_dev);
+    if (e == cudaSuccess)
+        e = cudaDeviceGetAttribute(&st->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, cur_dev);
     if (e == cudaSuccess && st->dm.tiled_ok) {
         switch (ellw) {
-            case 7: e = allow_tile_smem<7>(); break;
-            case 9: e = allow_tile_smem<9>(); break;
-            case 12: e = allow_tile_smem<12>(); break;
-            case 16: e = allow_tile_smem<16>(); break;
+            case 7: e = allow_tile_smem<7>(st->smem_optin); break;
+            case 9: e = allow_tile_smem<9>(st->smem_optin); break;
+            case 12: e = allow_tile_smem<12>(st->smem_optin); break;
+            case 16: e = allow_tile_smem<16>(st->smem_optin); break;
             default: break;
         }
     }
@@ -2367,8 +2386,9 @@ int felbm_sweep_tiled(felbm_state* st, int32_t on) {
         set_error("felbm_sweep_tiled: invalid argument (0 or 1)");
         return FELBM_ERR_INVALID_ARG;
     }
-    if (on && !st->dm.tiled_ok) {
-        set_error("felbm_sweep_tiled: this mesh has no ELL copy or a tile halo beyond the staged rows");
+    if (on && (!st->dm.tiled_ok || tile_parts(st, st->dm.ell_w) == 0)) {
+        set_error("felbm_sweep_tiled: this mesh has no ELL copy, a tile halo beyond the staged rows, or "
+                  "rows too long for two pipeline stages in shared memory");
         return FELBM_ERR_UNSUPPORTED;
     }
     FELBM_CUDA(cudaStreamSynchronize(st->stream));
@@ -2439,6 +2459,8 @@ int felbm_autotune(felbm_state* st, int32_t trials, felbm_tune_result* out) {
             for (int k = 0; k < 4 && rc == FELBM_OK; ++k) {
                 st->sweep_parts = parts_c[k];
                 st->sweep_tiled = tiled != 0;
+                // the tiled step runs 3 or 6 parts (two stages of 1 or 2 parts do not fit)
+                if (tiled && (tile_parts(st, st->dm.ell_w) != parts_c[k])) continue;
                 drop_graph(st);
                 float ms = 0.0f;
                 if ((rc = time_steps(st, trials, e0, e1, &ms)) != FELBM_OK) break;
