@@ -60,6 +60,10 @@ def parse():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--only-3d", action="store_true",
                     help="time only the 3D (D3Q19, tetrahedra) section and print it as one JSON line")
+    ap.add_argument("--ncu-case", choices=["fp32", "fp32-tiled", "fp64"],
+                    help="run two steps of the 1024-column rough-wall droplet (1,041,408 nodes, above L2, about "
+                         "2 GB on the device) and exit: the small case for ncu captures of the step kernels")
+    ap.add_argument("--sweep-parts", type=int, default=2, help="threads per node of the solve steps (--ncu-case)")
     return ap.parse_args()
 
 
@@ -196,6 +200,43 @@ def recorded_traffic(kernel, files=SOURCES_2D):
             if len(parts) >= 3 and not line.startswith("#") and parts[0] == kernel and parts[1] == h:
                 return float(parts[2])
     return None
+
+
+def recorded_fp64_flops(files=SOURCES_2D):
+    """FP64 flops per unit (triangle or node) of the FP64 step's kernels from
+    profiles/fp64_flops.txt (lines: kernel, source hash, flops, unit), for
+    these sources: 2 x DFMA + DADD + DMUL thread instructions of one ncu
+    capture divided by the units of the launch."""
+    path = os.path.join(ROOT, "profiles", "fp64_flops.txt")
+    out = {}
+    if not os.path.exists(path):
+        return out
+    h = source_hash(files)
+    with open(path) as f:
+        for line in f:
+            parts = line.split()
+            if len(parts) >= 4 and not line.startswith("#") and parts[1] == h:
+                out[parts[0]] = (float(parts[2]), parts[3])
+    return out
+
+
+def fp64_roofline(r64, n_nodes, n_tri, rate, fp64_peak, flops):
+    """FP64-pipe roofline of the FP64 step: the element kernel alone (the
+    largest FP64 kernel) and the whole step's FP64 flops per node-update."""
+    if not flops or "k_element" not in flops:
+        return {"bound": "fp64", "unavailable": "no FP64 flop counts recorded for these sources"}
+    per = {"tri": n_tri, "node": n_nodes}
+    ph = r64["phase_ms"]
+    el = flops["k_element"][0] * per[flops["k_element"][1]]
+    ach = el / (ph["element_ms"] * 1e-3) / 1e12
+    step = sum(f * per[u] * (2 if k == "k_refine" else 1) for k, (f, u) in flops.items()) / n_nodes
+    return {"bound": "fp64", "kernel": "k_element (P0 forces and element residual, FP64)",
+            "achieved": ach, "peak": fp64_peak, "unit": "TFLOP/s", "frac": ach / fp64_peak,
+            "flops_per_launch": el, "launch_ms": ph["element_ms"],
+            "step_fp64_flops_per_node_update": step,
+            "step_achieved": step * rate / 1e12, "step_frac": step * rate / 1e12 / fp64_peak,
+            "peak_source": "felbm_fp64_fma_rate (independent FP64 FMA chains on every SM, measured in this run)",
+            "source_hash": source_hash()}
 
 
 def peaks():
@@ -395,7 +436,7 @@ def time_adjoint(F, torch, dev, K):
             "adjoint_node_updates_per_s": n / (adj_ms * 1e-3), "adjoint_over_forward": adj_ms / fwd_ms}
 
 
-def time_free_droplet(F, torch, dev, K, flush, barrier, world, dist):
+def time_free_droplet(F, torch, dev, K, flush, barrier, world, dist, fp64_peak):
     """The 256 x 256 free droplet (131,072 nodes, 4 triangles per cell, jitter
     0.25h, density ratio 100, dt 0.05): FP32-deviation and FP64 steps.  Its
     solve working set fits in L2 inside a step."""
@@ -410,6 +451,9 @@ def time_free_droplet(F, torch, dev, K, flush, barrier, world, dist):
                      "phase_ms": {k: round(v, 5) for k, v in r["phase_ms"].items()},
                      "sweep_ms": r["phase_ms"]["solve_ms"] / r["solve_launches"], "autotune": r["tune"],
                      "finite": r["diag"]["status"] == 0}
+        if prec == F.FP64:
+            out[name]["fp64_roofline"] = fp64_roofline(r, n, len(w["mesh"]["tri"]), out[name]["value"] / world,
+                                                       fp64_peak, recorded_fp64_flops())
     return out
 
 
@@ -522,11 +566,12 @@ def run_gpu(args):
     N = len(w["mesh"]["xy"])
     K, W = args.steps, max(args.warmup, 3)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    fp64_peak = F.fp64_fma_rate()
     with ClockSampler(local) as clk:
         r32 = time_precision(F, torch, w, dev, F.FP32_DEV, K, W, flush, barrier, world, dist)
         r64 = time_precision(F, torch, w, dev, F.FP64, K, W, flush, barrier, world, dist)
         extra = not args.no_batch
-        rfd = time_free_droplet(F, torch, dev, K, flush, barrier, world, dist) if extra else None
+        rfd = time_free_droplet(F, torch, dev, K, flush, barrier, world, dist, fp64_peak) if extra else None
         rb = time_batch(F, torch, dev, max(10, K // 2), flush, barrier, world, dist) if extra else None
         radj = time_adjoint(F, torch, dev, max(5, K // 2)) if extra else None
         r3 = time_3d(torch, dev, max(5, K // 5), flush) if extra else None
@@ -564,6 +609,8 @@ def run_gpu(args):
                                                                     "wetted_length", "theta_deg", "status")}}
 
         s32, s64 = summary(r32, "f32 (FP64 C, mu, reductions)"), summary(r64, "f64")
+        s64["fp64_roofline"] = fp64_roofline(r64, N, len(w["mesh"]["tri"]), s64["value"] / world, fp64_peak,
+                                             recorded_fp64_flops())
         s64["e2e"] = {"value": s64["e2e_value"], "unit": "node-updates/s", "h2d_bytes_per_step": r64["state_bytes"],
                       "d2h_bytes_per_step": 8 * F.DIAG_SLOTS}
         nominal = 8000.0
@@ -636,8 +683,30 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
+def ncu_case(args):
+    """Two steps of the 1024-column rough-wall droplet in one precision, with
+    a fixed solve split (no autotuning, so the launches are the step's)."""
+    import torch
+    from paper_1708_04678_gb300 import build as B
+    B.build()
+    from paper_1708_04678_gb300 import felbm as F
+    from paper_1708_04678_gb300 import inputs as I
+    w = I.rough_wall_droplet(width=1024, R=150.0)
+    prec = F.FP64 if args.ncu_case == "fp64" else F.FP32_DEV
+    st = F.State(F.Mesh.from_dict(w["mesh"]), F.params_derive(w["phys"], precision=prec), w["C0"], device="cuda:0")
+    st.sweep_parts(args.sweep_parts)
+    if args.ncu_case == "fp32-tiled":
+        st.sweep_tiled(True)
+    st.step(2)
+    torch.cuda.synchronize()
+    print(json.dumps({"ncu_case": args.ncu_case, "nodes": len(w["mesh"]["xy"]), "status": st.diagnostics()["status"]}))
+
+
 def main():
     args = parse()
+    if args.ncu_case:
+        ncu_case(args)
+        return
     if args.cpu_baseline_only:
         v, n, secs = run_oracle(args.cpu_seconds, 10 ** 6, 1)
         print(json.dumps({"value": v, "unit": "node-updates/s", "cores": 1, "kind": "oracle",

@@ -47,6 +47,7 @@ extern "C" {
 #define FELBM_ERR_WORKSPACE (-4)    /* workspace missing, misaligned or too small */
 #define FELBM_ERR_NONFINITE (-5)    /* NaN or Inf found in the state */
 #define FELBM_ERR_UNSUPPORTED (-6)  /* option not available in this build */
+#define FELBM_ERR_NOT_CONVERGED (-7) /* the checked solve's residual is above its tolerance (felbm_solver_check) */
 
 #define FELBM_MAX_WALL_IDS 256
 
@@ -153,7 +154,10 @@ typedef struct felbm_diag {
     double wetted_length;     /* length of substrate wall edges with C >= 1/2 (linear in C) */
     double height;            /* max height of the C = 1/2 contour above the mean substrate height */
     double theta_deg;         /* contact angle from height and base, circular cap (Sec. III.B) */
-    int32_t status;           /* FELBM_OK or FELBM_ERR_NONFINITE */
+    int32_t status;           /* FELBM_OK, FELBM_ERR_NONFINITE or FELBM_ERR_NOT_CONVERGED */
+    int32_t solver_sweeps;    /* steps of one mass solve (all corrections) */
+    double solver_residual;   /* felbm_solver_check on: ||b - M x|| / ||b|| of the last solve before its
+                                 last step (all 18 right-hand sides); NaN when off */
 } felbm_diag;
 
 /* Text of the calling thread's last error ("" if none). */
@@ -216,12 +220,19 @@ void felbm_mesh_destroy(felbm_mesh* mesh);
 int felbm_workspace_bytes(const felbm_mesh* mesh, const felbm_params* params, size_t* bytes);
 
 /* Create a state on the device: upload the mesh tables into the workspace and
- * set g = w p, h = w C from C0 (double [n_nodes], host) with p = 0, u = 0 --
- * the equilibria at rest (eqn::g_eq, eqn::f_eq).  d_workspace: device
- * pointer, 256-byte aligned, >= felbm_workspace_bytes.  stream: cudaStream_t.
- * The mesh may be destroyed after this call.  Synchronises the stream. */
-int felbm_init(const felbm_mesh* mesh, const felbm_params* params, const double* C0,
-               void* d_workspace, size_t workspace_bytes, void* stream, felbm_state** out);
+ * set g, h to the equilibria of eqn::g_eq and eqn::f_eq at the initial
+ * fields: g = w p + rho cs2 (Gamma(u) - w), h = Gamma(u) C, with
+ * rho = C rho_l + (1 - C) rho_v.
+ *  C0  double [n_nodes] host, caller order (required)
+ *  p0  double [n_nodes] host or NULL (p = 0)
+ *  u0  double [2][n_nodes] host (u_x then u_y) or NULL (u = 0; the state
+ *      at rest, g = w p, h = w C)
+ * FP32_DEV states store C (FP64), p, u (rounded to FP32) and zero
+ * deviations.  d_workspace: device pointer, 256-byte aligned, >=
+ * felbm_workspace_bytes.  stream: cudaStream_t.  The mesh may be destroyed
+ * after this call.  Synchronises the stream. */
+int felbm_init(const felbm_mesh* mesh, const felbm_params* params, const double* C0, const double* p0,
+               const double* u0, void* d_workspace, size_t workspace_bytes, void* stream, felbm_state** out);
 
 /* Enqueue n_steps time steps (Sec. II.C): moments, chemical potential with the
  * wetting boundary (eqn:mp_mu, eqn:lapl_int_mp, eqn:bc2), element Laplacian of
@@ -262,6 +273,21 @@ int felbm_diag_finish(felbm_state* state, const felbm_diag_request* req, const d
  * meanwhile.  0 = tiled kernels for every member (default).  The step graph
  * is rebuilt at the next felbm_step.  Results do not depend on the schedule. */
 int felbm_batch_schedule(felbm_state* state, int32_t cta_max_nodes);
+
+/* Opt-in convergence check of the mass solve (Sec. II.C).  The solve runs a
+ * fixed number of steps (no residual is formed in the step itself); with the
+ * check on, every time step also computes, before the last step of its
+ * solve, the residual r = b - M x of the current iterate over all 18
+ * right-hand sides (b: the solve's right-hand side, carried through the
+ * corrections of the mixed solve), and felbm_diagnostics, felbm_diag_finish
+ * and felbm_diagnostics_groups report ||r|| / ||b|| of the last step's solve
+ * in solver_residual and return FELBM_ERR_NOT_CONVERGED (with the diagnostics
+ * filled, status = FELBM_ERR_NOT_CONVERGED) when it is above tol.  Costs one
+ * extra pass over the mesh per step.  With a CTA batch schedule it covers the
+ * members on the tiled kernels.  FELBM_ERR_UNSUPPORTED for the FP64 solver
+ * mode.  enable = 0 switches it off (tol ignored).  The step graph is
+ * rebuilt at the next felbm_step.  Synchronises. */
+int felbm_solver_check(felbm_state* state, int32_t enable, double tol);
 
 /* Threads per node of the FP32 solve sweeps (states with an FP32 solve):
  * 1, 2, 3 or 6, each owning 18 / parts of the node's right-hand sides.  Every
@@ -425,6 +451,14 @@ int felbm_timing_enable(felbm_state* state, int32_t enable);
  * its n_steps).  Synchronises the stream.  FELBM_ERR_INVALID_ARG if timing
  * is off or no step ran since it was switched on. */
 int felbm_timing_get(felbm_state* state, felbm_step_timing* out);
+
+/* Instrument: the FP64 FMA rate of the current device in TFLOP/s (2 flops
+ * per FMA), from the best of three timed launches of independent FMA chains
+ * on every SM, after a warm-up launch.  The roof of the kernels that the
+ * FP64 pipe bounds (the FP64 step's element and right-hand-side kernels).
+ * stream: cudaStream_t or NULL.  Synchronises the stream; allocates
+ * nothing. */
+int felbm_fp64_fma_rate(void* stream, double* tflops);
 
 /* Release the host-side state object (the caller frees the workspace). */
 void felbm_state_destroy(felbm_state* state);

@@ -24,7 +24,7 @@ its reason in the design notes of the repository):
   the incoming population psi_alpha is replaced by psi_opposite(alpha).
 * contact angle from height h and base b of the C = 1/2 contour:
   theta = atan2(b, 2 (r - h)), r = (4 h^2 + b^2) / (8 h).
-* initial state g = w p, h = w C (equilibrium at rest).
+* initial state: the equilibria of the initial C, p, u (g = w p, h = w C at rest).
 
 Parity status: every function here is pinned by ``tests/test_oracle_*.py``
 against closed forms, brute-force quadrature, invariants or physical laws
@@ -242,7 +242,7 @@ class OracleMesh:
 class OracleSim:
     """State (g, h) on an OracleMesh and the time step of Sec. II.C."""
 
-    def __init__(self, mesh: OracleMesh, params: OracleParams, C0, p0=None,
+    def __init__(self, mesh: OracleMesh, params: OracleParams, C0, p0=None, u0=None,
                  solver_tol=1e-14, solver_maxit=200):
         self.mesh = mesh
         self.prm = params
@@ -251,9 +251,11 @@ class OracleSim:
         N = mesh.N
         C0 = np.asarray(C0, dtype=np.float64)
         p0 = np.zeros(N) if p0 is None else np.asarray(p0, dtype=np.float64)
-        # initial state at rest: g = w p, h = w C (equilibria with u = 0)
-        self.g = D2Q9_W[:, None] * p0[None, :]
-        self.h = D2Q9_W[:, None] * C0[None, :]
+        u0 = np.zeros((N, 2)) if u0 is None else np.asarray(u0, dtype=np.float64).reshape(N, 2)
+        # initial state: the equilibria of the initial fields (at rest, u = 0,
+        # they are g = w p, h = w C)
+        rho0 = C0 * params.rho_l + (1.0 - C0) * params.rho_v
+        self.g, self.h = self.equilibria(C0, p0, u0, rho0)
         self.step_count = 0
         self.mass0 = self.mass()
         self.last_iters = 0
@@ -344,16 +346,24 @@ class OracleSim:
             Phi_h[a] = np.sum(em * vh, axis=1) * G[a] + pr.mobility * lmu * G[a]
         return Phi_g, Phi_h
 
-    # -- collision (eqn::collide) ------------------------------------------
-    def collide(self, g, h, C, p, u, rho):
-        pr = self.prm
-        inv_tau = C / pr.tau_l + (1.0 - C) / pr.tau_v
-        tau = 1.0 / inv_tau
+    # -- equilibria (eqn::g_eq, eqn::f_eq) ----------------------------------
+    @staticmethod
+    def equilibria(C, p, u, rho):
+        """g_eq = w (p + rho cs2 (e.u / cs2 + ((e.u)^2 - cs2 u.u) / (2 cs2^2)))
+        and h_eq = Gamma(u) C, each (9, N)."""
         eu = u @ D2Q9_E.T                                                  # (N, 9)
         uu = np.sum(u * u, axis=1)
         geq = D2Q9_W[:, None] * (p[None, :] + (rho * CS2)[None, :] * (
             eu.T / CS2 + (eu.T ** 2 - CS2 * uu[None, :]) / (2.0 * CS2 * CS2)))
         heq = gamma(u) * C[None, :]
+        return geq, heq
+
+    # -- collision (eqn::collide) ------------------------------------------
+    def collide(self, g, h, C, p, u, rho):
+        pr = self.prm
+        inv_tau = C / pr.tau_l + (1.0 - C) / pr.tau_v
+        tau = 1.0 / inv_tau
+        geq, heq = self.equilibria(C, p, u, rho)
         omega = 1.0 / (tau + 0.5)
         return g - omega[None, :] * (g - geq), h - omega[None, :] * (h - heq)
 

@@ -181,6 +181,7 @@ constexpr int kDiagBlocks = 304;   // fixed grid (2 x 152 SMs): the reduction or
 constexpr int kDiagSlots = 16;
 constexpr int kDiagSums = 13;        // slots of the final reduction (k_diag_final, or k_diag_fused32's last block)
 constexpr int kDiagStepSlot = 15;    // felbm_diagnostics_enqueue: the step count
+constexpr int kSolveResSlot = 13;    // slots 13, 14: sum r^2 and sum b^2 of the checked solve (felbm_solver_check)
 
 // ------------------------------------------------------ K1: collision -----
 // Moments of the pre-collision state (C = sum h, p = sum g, rho u = sum e g /
@@ -650,6 +651,59 @@ __global__ void __launch_bounds__(128) k_refine(DevMesh m, Bufs b, const float* 
     }
 }
 
+// -------------------------------------- solve residual (opt-in check) ----
+// Before the last step of the solve: sum over nodes and right-hand sides of
+// r^2, r = b_k - M x (FP32 rows, as the steps form them; b_k the current
+// correction's right-hand side), and of the solve's original right-hand
+// side squared (FP64 rhs for the mixed solve, the FP32 copy for FP32
+// storage).  Fixed grid, per-block partials, one ordered final sum: the
+// result does not depend on scheduling.
+template <bool kRhs64>
+__global__ void __launch_bounds__(kBlock) k_solve_resid(DevMesh m, Bufs b, const float* __restrict__ x,
+                                                        double* part) {
+    const int Np = m.Np;
+    double rr = 0.0, bb = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m.N; i += gridDim.x * blockDim.x) {
+        const int k0 = m.row_ptr[i], k1 = m.row_ptr[i + 1];
+        for (int q = 0; q < 18; ++q) {
+            float acc = 0.0f;
+            for (int k = k0; k < k1; ++k) acc = fmaf(m.mval32[k], x[q * Np + m.col[k]], acc);
+            const float r = b.r32[q * Np + i] - acc;
+            rr += (double)r * (double)r;
+            const double bq = kRhs64 ? b.rhs[q * Np + i] : (double)b.r32[q * Np + i];
+            bb += bq * bq;
+        }
+    }
+    __shared__ double sh[2][kBlock / 32];
+    for (int o = 16; o > 0; o >>= 1) {
+        rr += __shfl_down_sync(0xffffffffu, rr, o);
+        bb += __shfl_down_sync(0xffffffffu, bb, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        sh[0][threadIdx.x >> 5] = rr;
+        sh[1][threadIdx.x >> 5] = bb;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0, c = 0.0;
+        for (int w = 0; w < kBlock / 32; ++w) {
+            a += sh[0][w];
+            c += sh[1][w];
+        }
+        part[2 * blockIdx.x] = a;
+        part[2 * blockIdx.x + 1] = c;
+    }
+}
+__global__ void k_solve_resid_final(const double* __restrict__ part, int n, double* out) {
+    double a = 0.0, c = 0.0;
+    for (int k = 0; k < n; ++k) {
+        a += part[2 * k];
+        c += part[2 * k + 1];
+    }
+    out[0] = a;
+    out[1] = c;
+}
+
 // ----------------------------------------------- permutation kernels ------
 __global__ void k_scatter_in(DevMesh m, const double* __restrict__ stage, double* dst, int rows) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -668,16 +722,31 @@ __global__ void k_zero_rows(DevMesh m, double* dst, int row0, int row1) {
     if (i >= m.N) return;
     for (int q = row0; q < row1; ++q) dst[q * m.Np + i] = 0.0;
 }
-// initial state at rest: g = w p (p = 0), h = w C0
-__global__ void k_init_state(DevMesh m, const double* __restrict__ stage, double* psi) {
+// Initial state at equilibrium with the fields C0, p0, u0 (caller order in
+// stage: C0 [N], then p0 [N] if has_p, then u0 [2N] as x, y if has_u; the
+// missing ones are zero): g = w p + rho cs2 (Gamma(u) - w), h = Gamma(u) C
+// (eqn::g_eq, eqn::f_eq), rho = C rho_l + (1 - C) rho_v.
+__global__ void k_init_state(DevMesh m, Phys c, const double* __restrict__ stage, double* psi, int has_p,
+                             int has_u) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= m.N) return;
-    double C = stage[m.perm[i]];
-#pragma unroll
-    for (int q = 0; q < 9; ++q) {
-        psi[q * m.Np + i] = 0.0;
-        psi[(9 + q) * m.Np + i] = wq(q) * C;
+    const int o = m.perm[i], N = m.N;
+    const double C = stage[o];
+    const double p = has_p ? stage[N + o] : 0.0;
+    const double* u = stage + (has_p ? 2 : 1) * (size_t)N;
+    const double ux = has_u ? u[o] : 0.0, uy = has_u ? u[N + o] : 0.0;
+    const double rcs2 = (c.rho_v + C * (c.rho_l - c.rho_v)) * (1.0 / 3.0);
+    const double uu15 = 1.5 * (ux * ux + uy * uy);
+#define FELBM_INIT_Q(q)                                                      \
+    {                                                                        \
+        const double eu = edot<q>(ux, uy);                                   \
+        const double G = wq(q) * (1.0 + 3.0 * eu + 4.5 * eu * eu - uu15);    \
+        psi[q * m.Np + i] = wq(q) * p + rcs2 * (G - wq(q));                  \
+        psi[(9 + q) * m.Np + i] = G * C;                                     \
     }
+    FELBM_INIT_Q(0) FELBM_INIT_Q(1) FELBM_INIT_Q(2) FELBM_INIT_Q(3) FELBM_INIT_Q(4)
+    FELBM_INIT_Q(5) FELBM_INIT_Q(6) FELBM_INIT_Q(7) FELBM_INIT_Q(8)
+#undef FELBM_INIT_Q
 }
 
 // ------------------------------------------------------ diagnostics -------
@@ -1031,6 +1100,24 @@ __global__ void __launch_bounds__(kCtaThreads, 1) k_step_cta32(DevMesh m, Phys c
     }
 }
 
+// ------------------------------------------- FP64 FMA rate (instrument) --
+// Eight independent FP64 FMA chains per thread: the issue rate of the FP64
+// pipe, the roof of the FP64 kernels.  The result is stored only when it is
+// a value the chains cannot reach, so the work is kept but nothing is written.
+__device__ double g_fma_sink;
+__global__ void __launch_bounds__(256) k_fp64_fma_rate(int iters, double a) {
+    double x[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) x[k] = (double)(threadIdx.x + k) * 1e-3;
+    for (int it = 0; it < iters; ++it)
+#pragma unroll
+        for (int k = 0; k < 8; ++k) x[k] = fma(x[k], a, 1e-9);
+    double s = 0.0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) s += x[k];
+    if (s == -1.0) g_fma_sink = s;
+}
+
 // --------------------------------------------------------- host side ------
 static int cuda_fail(cudaError_t e, const char* what) {
     char buf[256];
@@ -1088,6 +1175,8 @@ struct felbm_state {
     bool use_pdl = true;  // programmatic dependent launch between solve sweeps
     int sweep_parts = 2;  // threads per node of the FP32 store sweeps (1, 2, 3, 6)
     bool sweep_tiled = false;  // store sweeps stage each node tile in shared memory (k_sweep_tile32)
+    bool check = false;        // felbm_solver_check: residual of every solve before its last step
+    double check_tol = 0.0;
     int n_sm = 1;              // multiprocessors of the device (grid of the persistent tiled step)
     int smem_optin = 0;        // largest dynamic shared memory a block may opt into
     felbm::GroupTables gt{};
@@ -1453,7 +1542,15 @@ static const double* enqueue_solve(felbm_state* st, const DevMesh& m, const Bufs
             const float tau = (float)st->tau[k];
             const bool last = r == st->rounds - 1 && k == st->sweeps - 1;
             // the previous launch is a sweep of this round, or a kernel that released its dependents
-            const bool pdl = k > 1 || (k == 1 && r == 0 && after_release);
+            bool pdl = k > 1 || (k == 1 && r == 0 && after_release);
+            if (last && st->check) {
+                if (st->dev32)
+                    k_solve_resid<false><<<kDiagBlocks, kBlock, 0, s>>>(m, b, cur, b.diag_part);
+                else
+                    k_solve_resid<true><<<kDiagBlocks, kBlock, 0, s>>>(m, b, cur, b.diag_part);
+                k_solve_resid_final<<<1, 1, 0, s>>>(b.diag_part, kDiagBlocks, b.diag_out + kSolveResSlot);
+                pdl = false;
+            }
             if (!last)
                 launch_sweep<kStore>(st, m, b, s, cur, prv, tau, have_x64, pdl);
             else if (!into_psi)
@@ -1582,8 +1679,8 @@ int felbm_workspace_bytes(const felbm_mesh* mesh, const felbm_params* params, si
     return FELBM_OK;
 }
 
-int felbm_init(const felbm_mesh* mesh, const felbm_params* params, const double* C0, void* d_workspace,
-               size_t workspace_bytes, void* stream, felbm_state** out) {
+int felbm_init(const felbm_mesh* mesh, const felbm_params* params, const double* C0, const double* p0,
+               const double* u0, void* d_workspace, size_t workspace_bytes, void* stream, felbm_state** out) {
     if (!mesh || !C0 || !out) {
         set_error("felbm_init: invalid argument");
         return FELBM_ERR_INVALID_ARG;
@@ -1836,12 +1933,23 @@ int felbm_init(const felbm_mesh* mesh, const felbm_params* params, const double*
     if (!dev32) UP(st->adj.kval, h.stiff);
 #undef UP
     if (e != cudaSuccess) return fail(e, "felbm_init: upload");
-    e = cudaMemcpyAsync(st->buf.stage, C0, sizeof(double) * h.N, cudaMemcpyHostToDevice, s);
-    if (e != cudaSuccess) return fail(e, "felbm_init: upload C0");
+    {
+        double* dst = st->buf.stage;
+        e = cudaMemcpyAsync(dst, C0, sizeof(double) * h.N, cudaMemcpyHostToDevice, s);
+        dst += h.N;
+        if (e == cudaSuccess && p0) {
+            e = cudaMemcpyAsync(dst, p0, sizeof(double) * h.N, cudaMemcpyHostToDevice, s);
+            dst += h.N;
+        }
+        if (e == cudaSuccess && u0) e = cudaMemcpyAsync(dst, u0, sizeof(double) * 2 * h.N, cudaMemcpyHostToDevice, s);
+    }
+    if (e != cudaSuccess) return fail(e, "felbm_init: upload C0, p0, u0");
     if (dev32)
-        k_init_dev32<<<grid_for(h.N, kBlock), kBlock, 0, s>>>(st->dm, st->buf, st->buf.stage);
+        k_init_dev32<<<grid_for(h.N, kBlock), kBlock, 0, s>>>(st->dm, st->buf, st->buf.stage, p0 != nullptr,
+                                                               u0 != nullptr);
     else
-        k_init_state<<<grid_for(h.N, kBlock), kBlock, 0, s>>>(st->dm, st->buf.stage, st->buf.psi);
+        k_init_state<<<grid_for(h.N, kBlock), kBlock, 0, s>>>(st->dm, st->phys, st->buf.stage, st->buf.psi,
+                                                               p0 != nullptr, u0 != nullptr);
     e = cudaGetLastError();
     if (e != cudaSuccess) return fail(e, "felbm_init: launch");
     e = cudaStreamSynchronize(s);
@@ -1970,6 +2078,40 @@ int felbm_timing_enable(felbm_state* st, int32_t enable) {
     return FELBM_OK;
 }
 
+int felbm_fp64_fma_rate(void* stream, double* tflops) {
+    if (!tflops) {
+        set_error("felbm_fp64_fma_rate: invalid argument");
+        return FELBM_ERR_INVALID_ARG;
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int dev = 0, n_sm = 0;
+    FELBM_CUDA(cudaGetDevice(&dev));
+    FELBM_CUDA(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
+    const int blocks = n_sm * 8, iters = 4096;
+    cudaEvent_t e0, e1;
+    FELBM_CUDA(cudaEventCreate(&e0));
+    FELBM_CUDA(cudaEventCreate(&e1));
+    float best = 1e30f;
+    for (int rep = 0; rep < 4; ++rep) {   // the first launch is a warm-up
+        cudaEventRecord(e0, s);
+        k_fp64_fma_rate<<<blocks, 256, 0, s>>>(iters, 0.999999);
+        cudaEventRecord(e1, s);
+        cudaError_t e = cudaEventSynchronize(e1);
+        float ms = 0.0f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e != cudaSuccess) {
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            return cuda_fail(e, "felbm_fp64_fma_rate");
+        }
+        if (rep > 0) best = std::min(best, ms);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    *tflops = 2.0 * 8.0 * iters * (double)blocks * 256.0 / (best * 1e-3) / 1e12;
+    return FELBM_OK;
+}
+
 int felbm_timing_get(felbm_state* st, felbm_step_timing* out) {
     if (!st || !out || !st->timing || !st->timed_step_ran) {
         set_error("felbm_timing_get: timing is off or no timed step ran");
@@ -2022,8 +2164,9 @@ static void enqueue_diag(felbm_state* st, const DiagReq& rq, cudaStream_t s) {
     k_diag_final<<<1, kDiagSums * 32, 0, s>>>(st->buf);
 }
 
+// res: the two sums of the solve check (sum r^2, sum b^2), read when it is on.
 static felbm_diag fill_diag(const felbm_state* st, const double* v, double mass0, int64_t nodes, int substrate,
-                            const int32_t* edges, int32_t n_edges, int64_t step) {
+                            const int32_t* edges, int32_t n_edges, int64_t step, const double* res) {
     const HostMesh& h = st->hm;
     felbm_diag d{};
     d.step = step;
@@ -2061,6 +2204,12 @@ static felbm_diag fill_diag(const felbm_state* st, const double* v, double mass0
         d.theta_deg = std::nan("");
     }
     d.status = v[9] > 0.0 ? FELBM_ERR_NONFINITE : FELBM_OK;
+    d.solver_sweeps = st->mode == FELBM_SOLVER_FP64 ? st->sweeps : st->sweeps * st->rounds;
+    d.solver_residual = std::nan("");
+    if (st->check && res) {
+        d.solver_residual = std::sqrt(res[0] / std::max(res[1], 1e-300));
+        if (d.status == FELBM_OK && !(d.solver_residual <= st->check_tol)) d.status = FELBM_ERR_NOT_CONVERGED;
+    }
     return d;
 }
 
@@ -2094,7 +2243,11 @@ int felbm_diagnostics(felbm_state* st, const felbm_diag_request* req, felbm_diag
     FELBM_CUDA(cudaMemcpyAsync(v, st->buf.diag_out, sizeof v, cudaMemcpyDeviceToHost, s));
     FELBM_CUDA(cudaStreamSynchronize(s));
     if (int rc = solve_status(st, "felbm_diagnostics")) return rc;
-    *out = fill_diag(st, v, st->mass0, st->hm.N, rq.substrate, nullptr, st->hm.E, st->step);
+    *out = fill_diag(st, v, st->mass0, st->hm.N, rq.substrate, nullptr, st->hm.E, st->step, v + kSolveResSlot);
+    if (out->status == FELBM_ERR_NOT_CONVERGED) {
+        set_error("felbm_diagnostics: the last solve's residual is above the tolerance of felbm_solver_check");
+        return FELBM_ERR_NOT_CONVERGED;
+    }
     if (out->status != FELBM_OK) {
         set_error("felbm_diagnostics: non-finite values in the state");
         return FELBM_ERR_NONFINITE;
@@ -2113,7 +2266,8 @@ int felbm_diagnostics_enqueue(felbm_state* st, const felbm_diag_request* req, do
     enqueue_diag(st, rq, s);
     FELBM_CUDA(cudaGetLastError());
     // the reduced sums arrive asynchronously; the step count is the host's now
-    FELBM_CUDA(cudaMemcpyAsync(slots, st->buf.diag_out, sizeof(double) * kDiagSums, cudaMemcpyDeviceToHost, s));
+    FELBM_CUDA(cudaMemcpyAsync(slots, st->buf.diag_out, sizeof(double) * (kSolveResSlot + 2), cudaMemcpyDeviceToHost,
+                               s));
     slots[kDiagStepSlot] = (double)st->step;
     return FELBM_OK;
 }
@@ -2125,7 +2279,11 @@ int felbm_diag_finish(felbm_state* st, const felbm_diag_request* req, const doub
     }
     const DiagReq rq = make_req(st, req);
     *out = fill_diag(st, slots, st->mass0, st->hm.N, rq.substrate, nullptr, st->hm.E,
-                     (int64_t)slots[kDiagStepSlot]);
+                     (int64_t)slots[kDiagStepSlot], slots + kSolveResSlot);
+    if (out->status == FELBM_ERR_NOT_CONVERGED) {
+        set_error("felbm_diag_finish: the last solve's residual is above the tolerance of felbm_solver_check");
+        return FELBM_ERR_NOT_CONVERGED;
+    }
     if (out->status != FELBM_OK) {
         set_error("felbm_diag_finish: non-finite values in the state");
         return FELBM_ERR_NONFINITE;
@@ -2153,19 +2311,26 @@ int felbm_diagnostics_groups(felbm_state* st, const felbm_diag_request* reqs, in
         k_diag_groups<false><<<n_groups, kBlock, 0, s>>>(st->dm, st->phys, st->buf, st->gt);
     FELBM_CUDA(cudaGetLastError());
     std::vector<double> v((size_t)n_groups * kDiagSlots);
+    double res[2] = {0.0, 0.0};
     FELBM_CUDA(cudaMemcpyAsync(v.data(), st->gt.out, sizeof(double) * v.size(), cudaMemcpyDeviceToHost, s));
+    FELBM_CUDA(cudaMemcpyAsync(res, st->buf.diag_out + kSolveResSlot, sizeof res, cudaMemcpyDeviceToHost, s));
     FELBM_CUDA(cudaStreamSynchronize(s));
-    bool bad = false;
+    bool bad = false, unconverged = false;
     for (int32_t g = 0; g < n_groups; ++g) {
         const double* vg = v.data() + (size_t)g * kDiagSlots;
         double m0 = g < (int32_t)st->gmass0.size() ? st->gmass0[g] : vg[0];
         out[g] = fill_diag(st, vg, m0, h.grp_size[g], rq[g].substrate, h.grp_wall_edge.data() + h.grp_wall_ptr[g],
-                           h.grp_wall_ptr[g + 1] - h.grp_wall_ptr[g], st->step);
-        bad = bad || out[g].status != FELBM_OK;
+                           h.grp_wall_ptr[g + 1] - h.grp_wall_ptr[g], st->step, res);
+        bad = bad || out[g].status == FELBM_ERR_NONFINITE;
+        unconverged = unconverged || out[g].status == FELBM_ERR_NOT_CONVERGED;
     }
     if (bad) {
         set_error("felbm_diagnostics_groups: non-finite values in the state");
         return FELBM_ERR_NONFINITE;
+    }
+    if (unconverged) {
+        set_error("felbm_diagnostics_groups: the last solve's residual is above the tolerance of felbm_solver_check");
+        return FELBM_ERR_NOT_CONVERGED;
     }
     return FELBM_OK;
 }
@@ -2377,6 +2542,24 @@ int felbm_batch_schedule(felbm_state* st, int32_t cta_max_nodes) {
     FELBM_CUDA(cudaStreamSynchronize(st->stream));
     int rc = set_schedule(st, cta_max_nodes);
     if (rc) return rc;
+    drop_graph(st);
+    return FELBM_OK;
+}
+
+int felbm_solver_check(felbm_state* st, int32_t enable, double tol) {
+    if (!st || (enable != 0 && enable != 1) || (enable && !(tol > 0.0))) {
+        set_error("felbm_solver_check: invalid argument (enable 0 or 1, tol > 0)");
+        return FELBM_ERR_INVALID_ARG;
+    }
+    if (enable && st->mode == FELBM_SOLVER_FP64) {
+        set_error("felbm_solver_check: needs the FP32 steps of the mixed or FP32-deviation solve");
+        return FELBM_ERR_UNSUPPORTED;
+    }
+    FELBM_CUDA(cudaStreamSynchronize(st->stream));
+    FELBM_CUDA(cudaMemsetAsync(st->buf.diag_out + kSolveResSlot, 0, 2 * sizeof(double), st->stream));
+    FELBM_CUDA(cudaStreamSynchronize(st->stream));
+    st->check = enable != 0;
+    st->check_tol = tol;
     drop_graph(st);
     return FELBM_OK;
 }

@@ -24,7 +24,7 @@ LAPMU_FACE, LAPMU_NODAL = 0, 1
 
 _ERRORS = {
     -1: "invalid argument", -2: "bad mesh", -3: "CUDA error", -4: "workspace",
-    -5: "non-finite state", -6: "unsupported",
+    -5: "non-finite state", -6: "unsupported", -7: "solve not converged",
 }
 
 
@@ -70,7 +70,8 @@ class Diag(ctypes.Structure):
                 ("max_u", ctypes.c_double), ("interface_rho_uu", ctypes.c_double),
                 ("p_in", ctypes.c_double), ("p_out", ctypes.c_double), ("delta_p", ctypes.c_double),
                 ("wetted_length", ctypes.c_double), ("height", ctypes.c_double),
-                ("theta_deg", ctypes.c_double), ("status", ctypes.c_int32)]
+                ("theta_deg", ctypes.c_double), ("status", ctypes.c_int32),
+                ("solver_sweeps", ctypes.c_int32), ("solver_residual", ctypes.c_double)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -121,7 +122,7 @@ def _declare(lib):
         "felbm_diagnostics_groups": (ctypes.c_int, [_P, _P, _I32, _P]),
         "felbm_workspace_bytes": (ctypes.c_int, [_P, ctypes.POINTER(Params),
                                                  ctypes.POINTER(ctypes.c_size_t)]),
-        "felbm_init": (ctypes.c_int, [_P, ctypes.POINTER(Params), _P, _P, ctypes.c_size_t, _P,
+        "felbm_init": (ctypes.c_int, [_P, ctypes.POINTER(Params), _P, _P, _P, _P, ctypes.c_size_t, _P,
                                       ctypes.POINTER(_P)]),
         "felbm_step": (ctypes.c_int, [_P, _I32]),
         "felbm_diagnostics": (ctypes.c_int, [_P, ctypes.POINTER(DiagRequest), ctypes.POINTER(Diag)]),
@@ -140,11 +141,13 @@ def _declare(lib):
         "felbm_batch_schedule": (ctypes.c_int, [_P, _I32]),
         "felbm_sweep_parts": (ctypes.c_int, [_P, _I32]),
         "felbm_sweep_tiled": (ctypes.c_int, [_P, _I32]),
+        "felbm_solver_check": (ctypes.c_int, [_P, _I32, ctypes.c_double]),
         "felbm_diagnostics_enqueue": (ctypes.c_int, [_P, ctypes.POINTER(DiagRequest), _P]),
         "felbm_diag_finish": (ctypes.c_int, [_P, ctypes.POINTER(DiagRequest), _P, ctypes.POINTER(Diag)]),
         "felbm_autotune": (ctypes.c_int, [_P, _I32, ctypes.POINTER(TuneResult)]),
         "felbm_timing_enable": (ctypes.c_int, [_P, _I32]),
         "felbm_timing_get": (ctypes.c_int, [_P, ctypes.POINTER(StepTiming)]),
+        "felbm_fp64_fma_rate": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double)]),
         "felbm_state_destroy": (None, [_P]),
     }
     for name, (res, args) in sig.items():
@@ -191,6 +194,14 @@ def _ptr(a):
             raise ValueError("array must be C-contiguous")
         return a.ctypes.data
     return a.data_ptr()
+
+
+def fp64_fma_rate(stream=None):
+    """felbm_fp64_fma_rate: the device's FP64 FMA rate in TFLOP/s (instrument)."""
+    v = ctypes.c_double()
+    _check(lib().felbm_fp64_fma_rate(ctypes.c_void_p(stream.cuda_stream) if stream is not None else None,
+                                     ctypes.byref(v)))
+    return v.value
 
 
 def params_derive(phys, lap_mode=LAP_CONSISTENT, solver_iters=0, precision=FP64,
@@ -297,9 +308,11 @@ class State:
     """felbm_state: the distributions and tables of one mesh on one GPU.
 
     The workspace is a torch uint8 tensor on ``device``; ``stream`` is a
-    ``torch.cuda.Stream`` (default: the current stream)."""
+    ``torch.cuda.Stream`` (default: the current stream).  The state starts at
+    the equilibria of C0, p0 (default 0) and u0 ((2, N) or (N, 2); default 0)."""
 
-    def __init__(self, mesh: Mesh, params: Params, C0, device="cuda", stream=None, workspace=None):
+    def __init__(self, mesh: Mesh, params: Params, C0, device="cuda", stream=None, workspace=None, p0=None,
+                 u0=None):
         import torch
         self.torch = torch
         self.params = params
@@ -314,9 +327,21 @@ class State:
         C0 = np.ascontiguousarray(C0, dtype=np.float64)
         if C0.shape != (self.N,):
             raise ValueError("C0 must have one value per node")
+        if p0 is not None:
+            p0 = np.ascontiguousarray(p0, dtype=np.float64)
+            if p0.shape != (self.N,):
+                raise ValueError("p0 must have one value per node")
+        if u0 is not None:
+            u0 = np.asarray(u0, dtype=np.float64)
+            if u0.shape == (self.N, 2):
+                u0 = u0.T
+            u0 = np.ascontiguousarray(u0)
+            if u0.shape != (2, self.N):
+                raise ValueError("u0 must have shape (2, N) or (N, 2)")
         h = _P()
-        _check(lib().felbm_init(mesh.handle, ctypes.byref(params), _ptr(C0), workspace.data_ptr(),
-                                nbytes, ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h)))
+        _check(lib().felbm_init(mesh.handle, ctypes.byref(params), _ptr(C0), _ptr(p0), _ptr(u0),
+                                workspace.data_ptr(), nbytes, ctypes.c_void_p(self.stream.cuda_stream),
+                                ctypes.byref(h)))
         self.handle = h
         self.n_groups = mesh.info()["n_groups"]
 
@@ -330,7 +355,7 @@ class State:
         req.radius, req.band, req.substrate_wall_id = float(radius), float(band), int(substrate)
         d = Diag()
         code = lib().felbm_diagnostics(self.handle, ctypes.byref(req), ctypes.byref(d))
-        if code not in (0, -5):
+        if code not in (0, -5, -7):
             _check(code)
         return d.as_dict()
 
@@ -354,7 +379,7 @@ class State:
         req = self._request(centre, radius, band, substrate)
         d = Diag()
         code = lib().felbm_diag_finish(self.handle, ctypes.byref(req), _ptr(slots), ctypes.byref(d))
-        if code not in (0, -5):
+        if code not in (0, -5, -7):
             _check(code)
         return d.as_dict()
 
@@ -374,7 +399,7 @@ class State:
                 reqs[g].substrate_wall_id = int(r.get("substrate", 0))
         out = (Diag * n_groups)()
         code = lib().felbm_diagnostics_groups(self.handle, reqs, n_groups, out)
-        if code not in (0, -5):
+        if code not in (0, -5, -7):
             _check(code)
         return [o.as_dict() for o in out]
 
@@ -474,6 +499,9 @@ class State:
 
     def sweep_tiled(self, on=True):
         _check(lib().felbm_sweep_tiled(self.handle, 1 if on else 0))
+
+    def solver_check(self, enable=True, tol=1e-6):
+        _check(lib().felbm_solver_check(self.handle, 1 if enable else 0, float(tol)))
 
     def autotune(self, trials=5):
         r = TuneResult()

@@ -384,3 +384,19 @@ def test_face_lapmu_has_growing_modes_nodal_does_not():
         prm = params_from_physical(_params(), lapmu=mode)
         ev = np.linalg.eigvals(_ch_operator(OracleSim(m, prm, np.full(m.N, 0.5)), m, prm))
         assert check(ev.real.max()), (mode, ev.real.max())
+
+
+def test_initial_state_has_the_given_moments():
+    """The initial state is the equilibrium of the given C0, p0, u0: its
+    moments return them exactly (sum h = C, sum g = p, sum e g = cs2 rho u)."""
+    m = _mesh(I.cross_mesh(5, 4, 0.2, 3))
+    prm = params_from_physical(_params())
+    rng = np.random.default_rng(8)
+    C0 = rng.uniform(0, 1, m.N)
+    p0 = rng.uniform(-0.01, 0.01, m.N)
+    u0 = rng.uniform(-0.05, 0.05, (m.N, 2))
+    sim = OracleSim(m, prm, C0, p0=p0, u0=u0)
+    C, p, u, rho = sim.moments()
+    np.testing.assert_allclose(C, C0, atol=1e-15)
+    np.testing.assert_allclose(p, p0, atol=1e-16)
+    np.testing.assert_allclose(u, u0, atol=1e-15)

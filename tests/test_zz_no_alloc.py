@@ -58,3 +58,34 @@ def test_static_solve_rejects_meshes_beyond_its_array():
     with pytest.raises(F.FelbmError) as e:
         gst.mass_solve_static(d_B, d_X)
     assert e.value.code == -4 and "static array" in str(e.value)
+
+
+def test_static_solve_overlapping_another_states_steps():
+    """Static solves of one state on its stream while another state takes
+    time steps on a second stream: neither touches the other's memory, so
+    both results are bit for bit those of the same work run one after the
+    other."""
+    import torch
+    w = I.sessile_droplet_64x32()
+    s_step, s_solve = torch.cuda.Stream(), torch.cuda.Stream()
+    a = gpu_state(w, stream=s_step)                     # takes the steps
+    b = gpu_state(w, stream=s_solve)                    # runs the static solves
+    ref = gpu_state(w)
+    ref.step(40)
+    g_ref, h_ref = ref.get_state()
+    rng = np.random.default_rng(11)
+    B = torch.from_numpy(rng.standard_normal((18, b.N))).cuda()
+    X_ref = torch.empty_like(B)
+    b.mass_solve_static(B, X_ref)
+    torch.cuda.synchronize()
+    X = [torch.full_like(B, float("nan")) for _ in range(8)]
+    torch.cuda.synchronize()
+    a.step(40)                                          # queued on s_step
+    for k in range(8):                                  # queued on s_solve meanwhile, one after another
+        b.mass_solve_static(B, X[k])
+    torch.cuda.synchronize()
+    g, h = a.get_state()
+    np.testing.assert_array_equal(g, g_ref)
+    np.testing.assert_array_equal(h, h_ref)
+    for k in range(8):
+        assert torch.equal(X[k], X_ref), k
