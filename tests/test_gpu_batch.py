@@ -126,3 +126,47 @@ def test_cta_schedule_matches_tiled_and_autotune_restores_state():
     assert rel_err(gc, ga) < 1e-6 and rel_err(hc, ha) < 1e-6
     dc = c.diagnostics_groups(_reqs(b))
     assert all(abs(d["mass_drift_rel"]) < 1e-6 for d in dc)
+
+
+def test_droplet_sweep_5000_steps_against_young_and_single_fp64_runs():
+    """The 64-droplet contact-angle sweep (widths 64..512, 3.46M nodes) for
+    its full 5,000 steps in FP32-deviation storage, in the launch
+    configuration the benchmark times (autotuned), with the nodal element
+    Laplacian of mu: the paper's face form diverges within 5,000 steps on
+    these jittered 2-triangle meshes (a growing Cahn-Hilliard mode; several
+    members, run alone in FP64, are non-finite by step 5,000).
+    At t = 1,250 the large droplets are still spreading, so Young's law is
+    checked as the direction and monotony of the motion: every contact angle
+    lies between the initial 90 degrees and its Young angle (within 1 degree),
+    and those more than 5 degrees from 90 approach the Young angle from 2,500
+    to 5,000 steps.  Eight members (the four narrowest,
+    two middle, the two widest) are run alone in FP64 for the same 5,000 steps:
+    the batch's FP32 angles agree with them to 0.5 degree."""
+    ws = I.droplet_sweep()
+    b = I.batch(ws)
+    st = F.State(F.Mesh.batch(b["meshes"]),
+                 F.params_derive(b["phys"], precision=F.FP32_DEV, lapmu_mode=F.LAPMU_NODAL), b["C0"])
+    st.autotune(trials=2)
+    reqs = [{"centre": m["centre"], "radius": m["R"], "band": 4.0, "substrate": m["substrate"]} for m in b["members"]]
+    st.step(2500)
+    mid = st.diagnostics_groups(reqs)
+    st.step(2500)
+    end = st.diagnostics_groups(reqs)
+    for k, (d0, d1) in enumerate(zip(mid, end)):
+        young = ws[k]["phys"]["theta_deg"][0]
+        assert d1["status"] == 0 and abs(d1["mass_drift_rel"]) < 1e-6, (k, d1)
+        assert min(90.0, young) - 1.0 <= d1["theta_deg"] <= max(90.0, young) + 1.0, (k, d1["theta_deg"], young)
+        if abs(young - 90.0) > 5.0:   # near 90 degrees the cap only rings about its angle
+            assert abs(d1["theta_deg"] - young) <= abs(d0["theta_deg"] - young) + 0.5, (k, d0["theta_deg"],
+                                                                                     d1["theta_deg"], young)
+    order = sorted(range(len(ws)), key=lambda k: ws[k]["mesh"]["period"][0])
+    for k in order[:4] + order[31:33] + order[-2:]:
+        w = ws[k]
+        one = F.State(F.Mesh.from_dict(w["mesh"]), F.params_derive(w["phys"], lapmu_mode=F.LAPMU_NODAL), w["C0"])
+        one.step(5000)
+        d = one.diagnostics(w["centre"], w["R"], 4.0, 0)
+        assert d["status"] == 0
+        assert abs(d["theta_deg"] - end[k]["theta_deg"]) < 0.5, (k, d["theta_deg"], end[k]["theta_deg"])
+        print(f"member {k}: W {int(w['mesh']['period'][0])}, Young {w['phys']['theta_deg'][0]:.1f}, "
+              f"batch FP32 {end[k]['theta_deg']:.4f}, single FP64 {d['theta_deg']:.4f}")
+        one.close()
