@@ -519,12 +519,12 @@ def time_3d(torch, dev, K, flush):
         if prec == F.FP32_DEV:
             sweeps = st.launches() - 4                       # mu, grad mu, element, rhs + the solve
             sweep_ms = ph["solve_ms"] / sweeps
-            # one sweep: gathered x_k, own x_{k-1}, rhs, new x (4 x 38 floats per
-            # node), the mass row (column + FP32 value per entry), 1/m_i per node
-            alg = n * (4 * 38 * 4 + 4) + info["nnz"] * (4 + 4)
+            # one solve step: gathered x_k, rhs, new x (3 x 38 floats per node),
+            # the mass row (column + FP32 value per entry), 1/m_i per node
+            alg = n * (3 * 38 * 4 + 4) + info["nnz"] * (4 + 4)
             hbm_peak, src = peaks()
             ach = alg / (sweep_ms * 1e-3) / 1e9
-            r["roofline"] = {"bound": "hbm", "kernel": "k3_sweep32 (one FP32 Chebyshev sweep, 38 RHS)",
+            r["roofline"] = {"bound": "hbm", "kernel": "k3_sweep32 (one step of the FP32 solve, 38 right-hand sides)",
                              "achieved": ach, "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak,
                              "traffic": recorded_traffic("k3_sweep32", SOURCES_3D),
                              "source_hash": source_hash(SOURCES_3D), "alg_bytes_per_launch": alg,
