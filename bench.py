@@ -82,7 +82,7 @@ def workload_config(w, world=1):
     """The `config` object of both arms: what the workload is."""
     return {"workload": "rough-wall droplet 2048x1024: wall y = 8 + 4 sin(2 pi x/64), 1017 body-fitted rows "
                         "(2,082,816 nodes, 4,161,536 triangles), jitter 0.2h, R 300, 60 deg, density ratio 100, "
-                        "dt 0.25",
+                        "dt 0.1",
             "nodes": len(w["mesh"]["xy"]), "triangles": len(w["mesh"]["tri"]), "dt": w["phys"]["dt"],
             "l2": "inputs larger than L2 (about 0.6 GB touched per solve step) and L2 flushed before every "
                   "timed step (256 MiB write)",

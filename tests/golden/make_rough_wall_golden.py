@@ -6,7 +6,7 @@ Runs the FP64 CPU oracle (``oracle/``, nothing else of this repository but
 the seeded input generator) for 20 time steps of the 2,082,816-node
 rough-wall droplet (width 2048, 1017 body-fitted rows on the wall
 y = 8 + 4 sin(2 pi x / 64), jitter 0.2h from seed 4, R 300, contact angle
-60 degrees, density ratio 100, dt 0.25) and stores g and h at a seeded
+60 degrees, density ratio 100, dt 0.1) and stores g and h at a seeded
 sample of nodes -- 4,096 drawn uniformly from default_rng(2024) plus every
 8th node of the rough wall -- with the global diagnostics, in
 ``rough_wall_20_steps.npz`` beside this script.  The oracle takes minutes
