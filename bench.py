@@ -20,9 +20,10 @@ The path has no exchange step across meshes, so N > 1 runs N independent
 replicas (one per GPU, weak scaling); value is the sum over ranks, the time
 the maximum over ranks.
 
-``--impl reference`` times the FP64 CPU oracle (numpy/scipy, one host core)
-on steps of a 128-column periodic strip of the same workload (130,176 nodes,
-the same rows, wall, jitter and physics), capped to about two minutes: one
+``--impl reference`` times the FP64 CPU oracle (numpy/scipy) on all host
+cores, one single-threaded process per core, each stepping its own copy of
+a 128-column periodic strip of the same workload (130,176 nodes, the same
+rows, wall, jitter and physics), capped to about two minutes: one
 step of the full mesh takes the oracle over a minute and several GB, and
 runs slower per node-update than the strip does (more cache misses), so the
 strip's rate is an upper bound on the oracle's full-mesh rate.
@@ -109,6 +110,89 @@ def run_oracle(budget_s, max_steps, warmup):
             break
     dt = time.perf_counter() - t0
     return len(m["xy"]) * n / dt, n, dt
+
+
+def _oracle_worker(conn):
+    """One host core of the all-cores oracle timing: builds its own copy of
+    the strip sample, then runs the number of steps it is sent and answers
+    with the wall time they took (None ends it)."""
+    from oracle import OracleMesh, OracleSim, params_from_physical
+    w = oracle_sample()
+    m = w["mesh"]
+    sim = OracleSim(OracleMesh(m["xy"], m["tri"], m["wall_edges"], m["wall_id"], m["period"]),
+                    params_from_physical(w["phys"]), w["C0"])
+    conn.send(len(m["xy"]))
+    while True:
+        k = conn.recv()
+        if k is None:
+            break
+        t0 = time.perf_counter()
+        sim.step(k)
+        conn.send(time.perf_counter() - t0)
+    conn.close()
+
+
+def host_procs():
+    """Processes for the all-cores oracle timing: one per usable host core,
+    capped so that their copies of the strip (about 0.75 GB each) fit in
+    half of the free host memory."""
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+    try:
+        free = os.sysconf("SC_AVPHYS_PAGES") * os.sysconf("SC_PAGE_SIZE")
+        cores = min(cores, max(1, int(free * 0.5 // (0.75 * 2 ** 30))))
+    except (ValueError, OSError):
+        pass
+    return max(1, min(cores, 64))
+
+
+def run_oracle_all_cores(budget_s, max_steps, warmup, procs):
+    """Time the FP64 oracle on all host cores at once: `procs` processes, one
+    per core and single-threaded, each stepping its own copy of the strip
+    sample (independent units, as the GPU replicas are).  The processes
+    advance in lock step, so each step costs the slowest one's time; returns
+    (node-updates/s over all processes, steps timed, seconds)."""
+    import multiprocessing as mp
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[k] = "1"                      # inherited by the spawned processes
+    ctx = mp.get_context("spawn")
+    pipes, workers = [], []
+    try:
+        for _ in range(procs):
+            a, b = ctx.Pipe()
+            p = ctx.Process(target=_oracle_worker, args=(b,), daemon=True)
+            p.start()
+            b.close()
+            pipes.append(a)
+            workers.append(p)
+        nodes = sum(c.recv() for c in pipes)
+
+        def lockstep():
+            for c in pipes:
+                c.send(1)
+            for c in pipes:
+                c.recv()
+
+        for _ in range(warmup):
+            lockstep()
+        t0 = time.perf_counter()
+        n = 0
+        while n < max_steps:
+            lockstep()
+            n += 1
+            if time.perf_counter() - t0 > budget_s:
+                break
+        dt = time.perf_counter() - t0
+    finally:
+        for c in pipes:
+            try:
+                c.send(None)
+            except (BrokenPipeError, OSError):
+                pass
+        for p in workers:
+            p.join(timeout=30)
+            if p.is_alive():
+                p.kill()
+    return nodes * n / dt, n, dt
 
 
 def cpu_baseline_subprocess(seconds):
@@ -667,17 +751,19 @@ def run_reference(args):
         return
     budget = 120.0
     warm = min(args.warmup, 1)
-    v, n, secs = run_oracle(budget, args.steps, warm)
+    procs = host_procs()
+    v, n, secs = run_oracle_all_cores(budget, args.steps, warm, procs)
     why = "the requested steps" if n >= args.steps else f"the first step past {budget:.0f} s"
-    sample = (f"{n} steps (after {warm} warm-up) of the 128-column strip of the rough-wall droplet "
-              f"(130,176 nodes, the same rows, wall, jitter and physics) in {secs:.1f} s (stopped after {why}); "
-              f"FP64 numpy/scipy oracle, one host core")
+    sample = (f"{n} steps (after {warm} warm-up) of {procs} copies of the 128-column strip of the rough-wall "
+              f"droplet (130,176 nodes each, the same rows, wall, jitter and physics), one single-threaded "
+              f"process per host core in lock step, in {secs:.1f} s (stopped after {why}); FP64 numpy/scipy "
+              f"oracle")
     out = {"metric": METRIC, "value": v, "unit": "node-updates/s", "n_gpus": world, "steps": n,
            "warmup": warm, "ms_per_step": secs * 1e3 / n, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": workload_config(workload(), world),
            "impl": "reference",
-           "cpu_baseline": {"value": v, "unit": "node-updates/s", "cores": 1, "kind": "oracle",
+           "cpu_baseline": {"value": v, "unit": "node-updates/s", "cores": procs, "kind": "oracle",
                             "sample": sample},
            "e2e": {"value": v, "unit": "node-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
@@ -708,11 +794,15 @@ def main():
         ncu_case(args)
         return
     if args.cpu_baseline_only:
-        v, n, secs = run_oracle(args.cpu_seconds, 10 ** 6, 1)
-        print(json.dumps({"value": v, "unit": "node-updates/s", "cores": 1, "kind": "oracle",
-                          "sample": f"{n} steps of the 128-column strip of the rough-wall droplet (130,176 "
-                                    f"nodes, the same rows, wall, jitter and physics) after 1 warm-up, {secs:.1f} s, "
-                                    f"numpy/scipy single thread"}))
+        v1, n1, s1 = run_oracle(args.cpu_seconds * 0.5, 10 ** 6, 1)
+        procs = host_procs()
+        v, n, secs = run_oracle_all_cores(args.cpu_seconds, 10 ** 6, 1, procs)
+        print(json.dumps({"value": v, "unit": "node-updates/s", "cores": procs, "kind": "oracle",
+                          "sample": f"{procs} single-threaded processes, one per host core, each stepping its "
+                                    f"own copy of the 128-column strip of the rough-wall droplet (130,176 nodes, "
+                                    f"the same rows, wall, jitter and physics) in lock step: {n} steps after 1 "
+                                    f"warm-up, {secs:.1f} s; FP64 numpy/scipy oracle",
+                          "single_core": {"value": v1, "steps": n1, "seconds": round(s1, 2)}}))
         return
     if args.impl == "reference":
         run_reference(args)
