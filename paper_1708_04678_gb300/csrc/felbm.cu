@@ -563,9 +563,9 @@ __global__ void __launch_bounds__(128) k_cheb32(DevMesh m, Phys c, Bufs b, const
 // (blockIdx.x = kParts * node block + part), so they run together and share
 // the block's matrix rows through L2 instead of fetching them from DRAM
 // once per part.
-template <int kFinal, int kW, int kParts>
+template <int kFinal, int kW, int kParts, bool kFromRhs = false>
 __global__ void __launch_bounds__(128) k_sweep32(DevMesh m, Phys c, Bufs b, const float* __restrict__ cur,
-                                                 float* nxt, float tau, int have_x64) {
+                                                 float* nxt, float tau, int have_x64, float tau0) {
     pdl_release();
     static_assert(kFinal != kUpdateDev || kParts == 1, "the field update needs the whole node");
     constexpr int NQ = 18 / kParts;
@@ -584,20 +584,38 @@ __global__ void __launch_bounds__(128) k_sweep32(DevMesh m, Phys c, Bufs b, cons
         }
     }
     const float s = tau * (i < m.N ? m.inv_lumped32[i] : 0.0f);
+    // kFromRhs: the first step of the solve, whose iterate x_0 = tau_0 b / m
+    // is formed here from the right-hand side (the RHS kernel stores b only)
+    float sc[kFromRhs ? kW : 1];
+    float s0 = 0.0f;
+    if constexpr (kFromRhs) {
+        if (i < m.N) {
+#pragma unroll
+            for (int k = 0; k < kW; ++k) sc[k] = m.inv_lumped32[col[k]] * tau0;
+            s0 = m.inv_lumped32[i] * tau0;
+        }
+    }
     pdl_wait();
     if (i >= m.N) return;
     // every gathered value is loaded before the first product (more loads in
     // flight per thread for this latency-bound gather: 15 % faster sweeps on
     // the 2.08M-node rough wall than interleaving loads and products)
     float g[kW][NQ], xk[NQ], rr[NQ];
+    const float* src = kFromRhs ? b.r32 : cur;
 #pragma unroll
     for (int k = 0; k < kW; ++k)
 #pragma unroll
-        for (int q = 0; q < NQ; ++q) g[k][q] = cur[(q0 + q) * Np + col[k]];
+        for (int q = 0; q < NQ; ++q) g[k][q] = src[(q0 + q) * Np + col[k]];
 #pragma unroll
     for (int q = 0; q < NQ; ++q) {
-        xk[q] = cur[(q0 + q) * Np + i];
         rr[q] = b.r32[(q0 + q) * Np + i];
+        xk[q] = kFromRhs ? rr[q] * s0 : cur[(q0 + q) * Np + i];
+    }
+    if constexpr (kFromRhs) {
+#pragma unroll
+        for (int k = 0; k < kW; ++k)
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) g[k][q] *= sc[k];
     }
     float d[NQ];
 #pragma unroll
@@ -1475,19 +1493,19 @@ static void launch_sweep_w(felbm_state* st, const DevMesh& m, const Bufs& b, cud
     const dim3 grid(grid_for(m.N, 128) * parts);
     switch (parts) {
         case 1:
-            launch_k(pdl, k_sweep32<kFinal, kW, 1>, grid, block, s, m, st->phys, b, cur, nxt, tau, have_x64);
+            launch_k(pdl, k_sweep32<kFinal, kW, 1>, grid, block, s, m, st->phys, b, cur, nxt, tau, have_x64, 0.0f);
             break;
         case 3:
             if constexpr (kFinal != kUpdateDev)
-                launch_k(pdl, k_sweep32<kFinal, kW, 3>, grid, block, s, m, st->phys, b, cur, nxt, tau, have_x64);
+                launch_k(pdl, k_sweep32<kFinal, kW, 3>, grid, block, s, m, st->phys, b, cur, nxt, tau, have_x64, 0.0f);
             break;
         case 6:
             if constexpr (kFinal != kUpdateDev)
-                launch_k(pdl, k_sweep32<kFinal, kW, 6>, grid, block, s, m, st->phys, b, cur, nxt, tau, have_x64);
+                launch_k(pdl, k_sweep32<kFinal, kW, 6>, grid, block, s, m, st->phys, b, cur, nxt, tau, have_x64, 0.0f);
             break;
         default:
             if constexpr (kFinal != kUpdateDev)
-                launch_k(pdl, k_sweep32<kFinal, kW, 2>, grid, block, s, m, st->phys, b, cur, nxt, tau, have_x64);
+                launch_k(pdl, k_sweep32<kFinal, kW, 2>, grid, block, s, m, st->phys, b, cur, nxt, tau, have_x64, 0.0f);
     }
 }
 
@@ -1513,13 +1531,49 @@ static void launch_sweep(felbm_state* st, const DevMesh& m, const Bufs& b, cudaS
     }
 }
 
+// The first step of the FP32 time-step solve with x_0 formed from b (gathered
+// ELL widths and the untiled steps only; false: not launched).
+template <int kW>
+static void launch_first_w(felbm_state* st, const DevMesh& m, const Bufs& b, cudaStream_t s, float* nxt,
+                           float tau, float tau0, bool pdl) {
+    const dim3 block(128);
+    const int parts = st->sweep_parts;
+    const dim3 grid(grid_for(m.N, 128) * parts);
+    switch (parts) {
+        case 1: launch_k(pdl, k_sweep32<kStore, kW, 1, true>, grid, block, s, m, st->phys, b, nullptr, nxt, tau, 0, tau0); break;
+        case 3: launch_k(pdl, k_sweep32<kStore, kW, 3, true>, grid, block, s, m, st->phys, b, nullptr, nxt, tau, 0, tau0); break;
+        case 6: launch_k(pdl, k_sweep32<kStore, kW, 6, true>, grid, block, s, m, st->phys, b, nullptr, nxt, tau, 0, tau0); break;
+        default: launch_k(pdl, k_sweep32<kStore, kW, 2, true>, grid, block, s, m, st->phys, b, nullptr, nxt, tau, 0, tau0);
+    }
+}
+
+static bool launch_first(felbm_state* st, const DevMesh& m, const Bufs& b, cudaStream_t s, float* nxt, float tau,
+                         float tau0, bool pdl) {
+    pdl = pdl && st->use_pdl;
+    switch (m.ell_w) {
+        case 7: launch_first_w<7>(st, m, b, s, nxt, tau, tau0, pdl); return true;
+        case 9: launch_first_w<9>(st, m, b, s, nxt, tau, tau0, pdl); return true;
+        case 12: launch_first_w<12>(st, m, b, s, nxt, tau, tau0, pdl); return true;
+        case 16: launch_first_w<16>(st, m, b, s, nxt, tau, tau0, pdl); return true;
+        default: return false;
+    }
+}
+
+// Whether the FP32 time step forms x_0 inside its first solve step (then the
+// RHS kernel stores b only): one correction round, gathered steps, at least
+// two steps after the first, no residual check, an ELL width with kernels.
+static bool first_from_rhs(const felbm_state* st, const DevMesh& m) {
+    return st->dev32 && st->rounds == 1 && st->sweeps > 2 && !st->check && !st->sweep_tiled &&
+           (m.ell_w == 7 || m.ell_w == 9 || m.ell_w == 12 || m.ell_w == 16);
+}
+
 // Enqueue the mass solve for the right-hand side in b.rhs (first iterate
-// already written).  into_psi: add the increment to psi (time step); else
+// already written, unless from_rhs).  into_psi: add the increment to psi (time step); else
 // leave the solution in x1/x0 (FP64 mode, returned) or x64 (mixed mode).
 // bufs: the buffers the solve reads and writes (the state's own, or another
 // set of scratch buffers with the same layout).
 static const double* enqueue_solve(felbm_state* st, const DevMesh& m, const Bufs& b, cudaStream_t s,
-                                   bool into_psi, bool after_release = false) {
+                                   bool into_psi, bool after_release = false, bool from_rhs = false) {
     const unsigned grid = grid_for(m.N, 128);
     if (st->mode == FELBM_SOLVER_FP64) {
         const double* result = b.x1;
@@ -1551,7 +1605,9 @@ static const double* enqueue_solve(felbm_state* st, const DevMesh& m, const Bufs
                 k_solve_resid_final<<<1, 1, 0, s>>>(b.diag_part, kDiagBlocks, b.diag_out + kSolveResSlot);
                 pdl = false;
             }
-            if (!last)
+            if (from_rhs && r == 0 && k == 1)
+                launch_first(st, m, b, s, prv, tau, (float)st->tau[0], pdl);
+            else if (!last)
                 launch_sweep<kStore>(st, m, b, s, cur, prv, tau, have_x64, pdl);
             else if (!into_psi)
                 launch_sweep<kAddX64>(st, m, b, s, cur, prv, tau, have_x64, pdl);
@@ -1624,14 +1680,24 @@ static void enqueue_step(felbm_state* st, cudaStream_t s) {
             mark(3);
             launch_k(chain, k_element32, dim3(grid_for(mt.T, 128)), dim3(128), s, mt, st->phys, b);
             mark(4);
-            switch (mt.iell_w) {
-                case 6: launch_k(chain, k_rhs32<6>, dim3(grid_for(mt.N, 128)), dim3(128), s, mt, st->phys, b, (float)st->tau[0]); break;
-                case 8: launch_k(chain, k_rhs32<8>, dim3(grid_for(mt.N, 128)), dim3(128), s, mt, st->phys, b, (float)st->tau[0]); break;
-                case 12: launch_k(chain, k_rhs32<12>, dim3(grid_for(mt.N, 128)), dim3(128), s, mt, st->phys, b, (float)st->tau[0]); break;
-                default: launch_k(chain, k_rhs32<0>, dim3(grid_for(mt.N, 128)), dim3(128), s, mt, st->phys, b, (float)st->tau[0]);
+            const bool from_rhs = first_from_rhs(st, mt);
+            const float tau0 = (float)st->tau[0];
+            const dim3 gn(grid_for(mt.N, 128)), bn(128);
+            switch (mt.iell_w * 2 + (from_rhs ? 1 : 0)) {
+                case 12: launch_k(chain, k_rhs32<6, true>, gn, bn, s, mt, st->phys, b, tau0); break;
+                case 13: launch_k(chain, k_rhs32<6, false>, gn, bn, s, mt, st->phys, b, tau0); break;
+                case 16: launch_k(chain, k_rhs32<8, true>, gn, bn, s, mt, st->phys, b, tau0); break;
+                case 17: launch_k(chain, k_rhs32<8, false>, gn, bn, s, mt, st->phys, b, tau0); break;
+                case 24: launch_k(chain, k_rhs32<12, true>, gn, bn, s, mt, st->phys, b, tau0); break;
+                case 25: launch_k(chain, k_rhs32<12, false>, gn, bn, s, mt, st->phys, b, tau0); break;
+                default:
+                    if (from_rhs)
+                        launch_k(chain, k_rhs32<0, false>, gn, bn, s, mt, st->phys, b, tau0);
+                    else
+                        launch_k(chain, k_rhs32<0, true>, gn, bn, s, mt, st->phys, b, tau0);
             }
             mark(5);
-            enqueue_solve(st, mt, st->buf, s, true, chain);
+            enqueue_solve(st, mt, st->buf, s, true, chain, from_rhs);
         } else {
             mark(2);
             mark(3);

@@ -242,7 +242,7 @@ __global__ void __launch_bounds__(128, 6) k_element32(DevMesh m, Phys c, Bufs b)
 //                h: -6 w C (e.u)   + (1-omega)(dh_opp - dh).
 // kI > 0: the incident triangles from the incidence ELL (padding: the zero
 // residual row T), their ids and gradients loaded up front; kI = 0: CSR.
-template <int kI = 0>
+template <int kI = 0, bool kFirst = true>
 __device__ __forceinline__ void rhs32_node(const DevMesh& m, const Phys& c, const Bufs& b, int i, float tau0) {
     const int Np = m.Np;
     float acc[18];
@@ -326,17 +326,17 @@ __device__ __forceinline__ void rhs32_node(const DevMesh& m, const Phys& c, cons
 #pragma unroll
     for (int q = 0; q < 18; ++q) {
         b.r32[q * Np + i] = acc[q];
-        b.e1[q * Np + i] = acc[q] * s;
+        if (kFirst) b.e1[q * Np + i] = acc[q] * s;
     }
 }
 
 // at most 64 registers (8 blocks of 128 per SM; 6 % faster than 96 registers)
-template <int kI>
+template <int kI, bool kFirst = true>
 __global__ void __launch_bounds__(128, 8) k_rhs32(DevMesh m, Phys c, Bufs b, float tau0) {
     pdl_release();
     pdl_wait();
     int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < m.N) rhs32_node<kI>(m, c, b, i, tau0);
+    if (i < m.N) rhs32_node<kI, kFirst>(m, c, b, i, tau0);
 }
 
 // ---------------------------- update of fields and deviations (node) ------
