@@ -158,7 +158,7 @@ struct Bufs {
     float* e0;       // [18][Np] FP32 Chebyshev iterates
     float* e1;
     // FP32-deviation storage (precision FELBM_FP32_DEV); C above stays FP64
-    float* dpsi;     // [18][Np] deviations from equilibrium
+    float* dpsi;     // deviations from equilibrium: [Np][16] rows (q = 1..8 of g, h), then [2][Np] (q = 0)
     float* p32;      // [Np]
     float* ux32;
     float* uy32;
@@ -852,7 +852,7 @@ __device__ __forceinline__ void diag_node(const DevMesh& m, const Phys& c, const
         ruu = rhof * uuf;
         float dsum = 0.0f;
 #pragma unroll
-        for (int q = 0; q < 18; ++q) dsum += b.dpsi[q * Np + i];
+        for (int q = 0; q < 18; ++q) dsum += b.dpsi[dpsi_at(Np, q, i)];
         // non-finite deviations are reported too
         finite = finite_bits(C) && isfinite(b.p32[i]) && isfinite(uuf) && isfinite(dsum);
     } else {
