@@ -608,9 +608,10 @@ def time_3d(torch, dev, K, flush):
             alg = n * (3 * 38 * 4 + 4) + info["nnz"] * (4 + 4)
             hbm_peak, src = peaks()
             ach = alg / (sweep_ms * 1e-3) / 1e9
-            r["roofline"] = {"bound": "hbm", "kernel": "k3_sweep32 (one step of the FP32 solve, 38 right-hand sides)",
+            r["roofline"] = {"bound": "hbm", "kernel": "k3_sweep_rows32 (one step of the FP32 solve, 38 right-hand "
+                                                       "sides, ten lanes per node)",
                              "achieved": ach, "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak,
-                             "traffic": recorded_traffic("k3_sweep32", SOURCES_3D),
+                             "traffic": recorded_traffic("k3_sweep_rows32", SOURCES_3D),
                              "source_hash": source_hash(SOURCES_3D), "alg_bytes_per_launch": alg,
                              "launch_ms": sweep_ms, "peak_source": src}
         out[name] = r
