@@ -177,7 +177,7 @@ struct Bufs {
 };
 
 constexpr int kBlock = 256;
-constexpr int kDiagBlocks = 304;   // fixed grid (2 x 152 SMs): the reduction order never changes
+constexpr int kDiagBlocks = 608;   // fixed grid (4 x 152 SMs): the reduction order never changes
 constexpr int kDiagSlots = 16;
 constexpr int kDiagSums = 13;        // slots of the final reduction (k_diag_final, or k_diag_fused32's last block)
 constexpr int kDiagStepSlot = 15;    // felbm_diagnostics_enqueue: the step count

@@ -414,10 +414,12 @@ __device__ __forceinline__ void dev32_update(const DevMesh& m, const Phys& c, co
 
 // ------------------------------------ conversions to / from full FP64 ------
 // stage [18][N] (caller order) <- psi = psi^eq(C, p, u) + dpsi, in FP64
+// (one thread per caller-order node o: the 18 stage streams are written
+// coalesced, the node's fields and deviation row read at i = iperm[o])
 __global__ void k_dev32_to_full(DevMesh m, Phys c, Bufs b, double* stage) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= m.N) return;
-    const int N = m.N, Np = m.Np, o = m.perm[i];
+    const int o = blockIdx.x * blockDim.x + threadIdx.x;
+    if (o >= m.N) return;
+    const int N = m.N, Np = m.Np, i = m.iperm[o];
     double C = b.C[i], p = b.p32[i], ux = b.ux32[i], uy = b.uy32[i];
     double rho = c.rho_v + C * (c.rho_l - c.rho_v);
     double uu15 = 1.5 * (ux * ux + uy * uy);
@@ -431,10 +433,12 @@ __global__ void k_dev32_to_full(DevMesh m, Phys c, Bufs b, double* stage) {
 }
 
 // fields and deviations <- psi (stage [18][N], caller order, FP64)
+// (one thread per caller-order node o: the 18 stage streams are read
+// coalesced, the node's fields and deviation row written at i = iperm[o])
 __global__ void k_full_to_dev32(DevMesh m, Phys c, Bufs b, const double* __restrict__ stage) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= m.N) return;
-    const int N = m.N, Np = m.Np, o = m.perm[i];
+    const int o = blockIdx.x * blockDim.x + threadIdx.x;
+    if (o >= m.N) return;
+    const int N = m.N, Np = m.Np, i = m.iperm[o];
     double g[9], h[9], C = 0.0, p = 0.0;
 #pragma unroll
     for (int q = 0; q < 9; ++q) {
