@@ -61,9 +61,9 @@ __device__ __forceinline__ void mu32_node(const DevMesh& m, const Phys& c, const
     b.mu32[i] = (float)(2.0 * c.beta * Ci * (Ci - 1.0) * (2.0 * Ci - 1.0) - (c.kappa * lap + wall * m.inv_vol[i]));
 }
 
-// kW > 0: the same sum over the ELL copy of the row (same order, zero
-// padding), its columns and coefficients loaded up front so the gathers of
-// C are issued together; kW = 0: CSR.
+// kW > 0: the sum over the ELL copy of the row (zero padding), its columns
+// and coefficients loaded up front so the gathers of C are issued together;
+// kW = 0: CSR, in the difference form of the FP64 path.
 template <int kW>
 __global__ void __launch_bounds__(kBlock) k_mu32(DevMesh m, Phys c, Bufs b) {
     pdl_release();
@@ -80,10 +80,15 @@ __global__ void __launch_bounds__(kBlock) k_mu32(DevMesh m, Phys c, Bufs b) {
             col[k] = m.ell_col[k * Np + i];
             l[k] = m.ell_lval[k * Np + i];
         }
+        // The row's coefficients sum to zero (the P1 stiffness rows do), so
+        // sum l_k (C_k - C_i) = sum l_k C_k: one FP64 FMA per entry instead
+        // of a subtraction and an FMA on this FP64-pipe-bound kernel.  The
+        // cancellation costs about 1e-15 absolute in the Laplacian, far below
+        // the FP32 rounding of the stored mu.
         const double Ci = b.C[i];
         double lap = 0.0;
 #pragma unroll
-        for (int k = 0; k < kW; ++k) lap += l[k] * (b.C[col[k]] - Ci);
+        for (int k = 0; k < kW; ++k) lap = fma(l[k], b.C[col[k]], lap);
         double wall = 0.0;
         for (int k = m.winc_ptr[i]; k < m.winc_ptr[i + 1]; ++k) {
             int e = m.winc_edge[k];
