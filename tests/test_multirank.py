@@ -48,3 +48,16 @@ def test_reference_arm_runs_on_rank_zero_only():
     r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
                         "--warmup", "0"], capture_output=True, text=True, env=env, timeout=120)
     assert r.returncode == 0 and r.stdout.strip() == ""
+
+
+def test_oracle_timing_on_several_host_cores():
+    """The CPU baseline's all-cores form: one single-threaded oracle process
+    per core, each on its own copy of the strip sample, stepped in lock step;
+    the rate counts every process's node-updates."""
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.host_procs() >= 1
+    v, n, secs = bench.run_oracle_all_cores(1.0, 1, 0, 2)
+    nodes = len(bench.oracle_sample()["mesh"]["xy"])
+    assert n == 1 and secs > 0.0
+    assert v == pytest.approx(2 * nodes * n / secs)
