@@ -1531,8 +1531,11 @@ static void launch_sweep(felbm_state* st, const DevMesh& m, const Bufs& b, cudaS
     }
 }
 
+// ELL widths with compiled gathered solve steps
+static bool gathered_width(int ell_w) { return ell_w == 7 || ell_w == 9 || ell_w == 12 || ell_w == 16; }
+
 // The first step of the FP32 time-step solve with x_0 formed from b (gathered
-// ELL widths and the untiled steps only; false: not launched).
+// ELL widths and the untiled steps only).
 template <int kW>
 static void launch_first_w(felbm_state* st, const DevMesh& m, const Bufs& b, cudaStream_t s, float* nxt,
                            float tau, float tau0, bool pdl) {
@@ -1547,15 +1550,15 @@ static void launch_first_w(felbm_state* st, const DevMesh& m, const Bufs& b, cud
     }
 }
 
-static bool launch_first(felbm_state* st, const DevMesh& m, const Bufs& b, cudaStream_t s, float* nxt, float tau,
+// Only called when gathered_width(m.ell_w) (first_from_rhs checks it).
+static void launch_first(felbm_state* st, const DevMesh& m, const Bufs& b, cudaStream_t s, float* nxt, float tau,
                          float tau0, bool pdl) {
     pdl = pdl && st->use_pdl;
     switch (m.ell_w) {
-        case 7: launch_first_w<7>(st, m, b, s, nxt, tau, tau0, pdl); return true;
-        case 9: launch_first_w<9>(st, m, b, s, nxt, tau, tau0, pdl); return true;
-        case 12: launch_first_w<12>(st, m, b, s, nxt, tau, tau0, pdl); return true;
-        case 16: launch_first_w<16>(st, m, b, s, nxt, tau, tau0, pdl); return true;
-        default: return false;
+        case 7: launch_first_w<7>(st, m, b, s, nxt, tau, tau0, pdl); break;
+        case 9: launch_first_w<9>(st, m, b, s, nxt, tau, tau0, pdl); break;
+        case 12: launch_first_w<12>(st, m, b, s, nxt, tau, tau0, pdl); break;
+        default: launch_first_w<16>(st, m, b, s, nxt, tau, tau0, pdl);
     }
 }
 
@@ -1564,7 +1567,7 @@ static bool launch_first(felbm_state* st, const DevMesh& m, const Bufs& b, cudaS
 // two steps after the first, no residual check, an ELL width with kernels.
 static bool first_from_rhs(const felbm_state* st, const DevMesh& m) {
     return st->dev32 && st->rounds == 1 && st->sweeps > 2 && !st->check && !st->sweep_tiled &&
-           (m.ell_w == 7 || m.ell_w == 9 || m.ell_w == 12 || m.ell_w == 16);
+           gathered_width(m.ell_w);
 }
 
 // Enqueue the mass solve for the right-hand side in b.rhs (first iterate
