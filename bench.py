@@ -480,13 +480,26 @@ def time_batch(F, torch, dev, K, flush, barrier, world, dist):
             for m in b["members"]]
     dg = st.diagnostics_groups(reqs)
     n = mesh.info()["n_nodes"]
+    st.timing_enable(True)
+    st.step(1)
+    sweeps = st.timing_get()["solve_launches"] + 1
+    st.timing_enable(False)
     st.close()
+    value = job_rate(n, K, world, total_ms)
+    # the whole step against the minimum bytes per node-update of the FP32
+    # form, as for the rough wall (distributions and right-hand side written
+    # and read, three 18-float streams per solve step, ~200 B of fields)
+    step_bytes = 2 * 18 * 4 + 2 * 18 * 4 + sweeps * 3 * 18 * 4 + 200
+    hbm_peak, peak_src = peaks()
     return {"workload": "64-droplet contact-angle sweep, widths 64..512, FP32 deviation storage",
             "nodes": n, "members": len(b["members"]), "steps": K,
-            "value": job_rate(n, K, world, total_ms), "unit": "node-updates/s",
+            "value": value, "unit": "node-updates/s",
             "ms_per_step": total_ms / K, "schedule": tune,
             "finite": all(d["status"] == 0 for d in dg),
-            "max_abs_mass_drift_rel": max(abs(d["mass_drift_rel"]) for d in dg)}
+            "max_abs_mass_drift_rel": max(abs(d["mass_drift_rel"]) for d in dg),
+            "step_roofline": {"alg_bytes_per_node_update": step_bytes, "sweeps": sweeps,
+                              "achieved": value / world * step_bytes / 1e9, "peak": hbm_peak, "unit": "GB/s",
+                              "frac": value / world * step_bytes / 1e9 / hbm_peak, "peak_source": peak_src}}
 
 
 def time_adjoint(F, torch, dev, K):
