@@ -180,6 +180,28 @@ def test_channel_mesh_with_a_hole(lib):
     assert info["n_groups"] == 1
 
 
+def test_capillary_intrusion_workload(lib):
+    """The capillary-intrusion workload: the channel geometry at H = 16 with
+    the physics that lets the contact line move (xi 4, M 1, dt 0.05), the
+    liquid column ending 2H inside the channel on its centre line, and a
+    mesh the library accepts with the block's perimeter as walls."""
+    w = I.capillary_intrusion(H=16, theta=56.0)
+    ph = w["phys"]
+    assert (ph["xi"], ph["mobility"], ph["dt"], ph["theta_deg"]) == (4.0, 1.0, 0.05, (56.0,))
+    xy, C0 = w["mesh"]["xy"], w["C0"]
+    line = np.abs(xy[:, 1] - w["y_c"]) < 0.25
+    x, c = xy[line, 0], C0[line]
+    o = np.argsort(x)
+    x, c = x[o], c[o]
+    inside = (x > w["x_in"]) & (x < w["x_in"] + w["length"])
+    j = np.nonzero(inside & (c > 0.5))[0][-1]
+    cross = x[j] + (c[j] - 0.5) / (c[j] - c[j + 1]) * (x[j + 1] - x[j])
+    assert abs(cross - (w["x_in"] + 2 * w["H"])) < 1e-9
+    info = F.Mesh.from_dict(w["mesh"]).info()
+    assert info["n_nodes"] == len(xy) == 11615
+    assert info["n_wall_edges"] == 2 * int(w["length"]) + 2 * (2 * 16)
+
+
 def test_node_tiles_of_the_workloads():
     """Tiles cover every node with at most 1024 nodes and a halo that fits the
     staged rows of the tiled solve step (504), on the rough-wall droplet, the
