@@ -33,3 +33,13 @@ def compare_states(osim, gst):
     g, h = gst.get_state()
     return {"g": rel_err(g, osim.g), "h": rel_err(h, osim.h),
             "C": rel_err(h.sum(0), osim.h.sum(0))}
+
+
+def elementwise_c_err(osim, gst, floor=0.05):
+    """Largest elementwise relative error of C = sum h over the nodes where
+    the oracle's C is at least `floor` (where a ratio means something)."""
+    h = gst.get_state()[1]
+    C, Co = h.sum(0), osim.h.sum(0)
+    sel = np.abs(Co) >= floor
+    return float((np.abs(C[sel] - Co[sel]) / np.abs(Co[sel])).max())
+

@@ -15,7 +15,7 @@ import pytest
 
 from paper_1708_04678_gb300 import felbm as F
 from paper_1708_04678_gb300 import inputs as I
-from parity_util import compare_states, gpu_state, oracle_sim, rel_err
+from parity_util import compare_states, elementwise_c_err, gpu_state, oracle_sim, rel_err
 
 pytestmark = pytest.mark.gpu
 TOL = 1e-11
@@ -117,6 +117,9 @@ def test_sessile_droplet_64x32_full_run():
     gst.step(w["steps"])
     err = compare_states(osim, gst)
     assert max(err.values()) < TOL, err
+    ce = elementwise_c_err(osim, gst)
+    print(f"elementwise relative C error over C >= 0.05: {ce:.2e}")
+    assert ce < TOL, ce
     dg = gst.diagnostics(w["centre"], w["R"], 4.0, 0)
     do = osim.diagnostics(w["centre"], w["R"], 4.0, 0)
     assert abs(dg["mass_drift_rel"]) < 1e-12 and abs(do["mass_drift_rel"]) < 1e-12
@@ -135,6 +138,9 @@ def test_free_droplet_256_full_size():
     gst.step(20)
     err = compare_states(osim, gst)
     assert max(err.values()) < TOL, err
+    ce = elementwise_c_err(osim, gst)
+    print(f"elementwise relative C error over C >= 0.05: {ce:.2e}")
+    assert ce < TOL, ce
 
 
 def test_rough_wall_full_size_properties():
